@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput benchmark: batched Frenkel-Ladd switching of 8000-atom diamond silicon.
+
+Workload (per GPU): R replicas of an 8000-atom Si-cd crystal (10x10x10 cells, a = 5.431 A,
+standard SW), Frenkel-Ladd switching to an Einstein crystal (k = 5 eV/A^2, lambda(tau) =
+tau^5(70tau^4-315tau^3+540tau^2-420tau+126), 20000 steps per direction, half the replicas
+forward and half backward) at 1000 K with a Langevin thermostat (0.1 ps), dt = 1 fs, FP32
+pair/triplet arithmetic with FP64 positions, box, energies and work.  Inputs are synthetic
+and seeded.  One timed step = one replay of the captured 32-MD-step graph over all
+replicas (every MD step runs the whole path: group update, kick/drift, list rebuild when
+the displacement test fires, forces with lambda mixing, Langevin, kick, work).
+
+Prints one JSON line (see the keys below).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (batched FP32/FP64 vs plain FP64, 1 GB300), % HBM roofline, ΔG err"
+UNIT = "atom-steps/s"
+KB = 8.617333262e-5
+MVV2E = 1.66053906660e-23 / 1.602176634e-19
+MASS = 28.0855
+NCELL = 10          # 10x10x10 diamond cells = 8000 atoms
+T_SW = 1000.0
+K_E = 5.0
+NSCHED = 20000
+MD_STEPS = 32       # MD steps per timed step (one graph replay)
+# Algorithmic bytes of the force kernel per atom (FP32 path, Frenkel-Ladd): own mirror 16,
+# count 4, neighbour row 4 * nbar, x 24, r0 24, v read 24, v write 24, F write 16.
+FORCE_FIXED_BYTES = 16 + 4 + 24 + 24 + 24 + 24 + 16
+
+
+def workload_config(replicas):
+    return {"workload": f"Frenkel-Ladd switching, {replicas} x 8000-atom Si-cd (SW), 1000 K, k=5 eV/A^2",
+            "atoms_per_replica": 8 * NCELL ** 3, "replicas_per_gpu": replicas,
+            "md_steps_per_step": MD_STEPS, "dt_fs": 1.0, "switch_steps": NSCHED,
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2103_10449_gb300", "csrc", "nefe_kernels.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per atom of the force kernel from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_force_fl8000_traffic.txt")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*(\w+)", txt)
+    b = re.search(r"dram_bytes_per_atom:\s*([0-9.eE+-]+)", txt)
+    if not m or not b or m.group(1) != kernel_hash():
+        return None
+    return float(b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_context(N, replicas, precision, seed0=1000, stream=None):
+    from paper_2103_10449_gb300 import inputs as I
+    x, box = I.diamond(NCELL, NCELL, NCELL)
+    sv = math.sqrt(KB * T_SW / (MASS * MVV2E))
+    ctx = N.Context(precision=precision, dt=0.001, skin=0.5, nbr_cap=48, stream=stream)
+    for r in range(replicas):
+        v = I.gaussian_velocities(len(x), sv, seed0 + r)
+        s = ctx.add_system(x, box, v=v, r0=x, mass=MASS)
+        ctx.set_thermostat(s, T_SW, 0.1, seed0 + r)
+        ctx.set_schedule(s, N.NEFE_SCHED_FL, direction=1 if r % 2 == 0 else -1, nsteps=NSCHED, k_E=K_E)
+    ctx.setup()
+    return ctx, len(x)
+
+
+def time_steps(torch, ctx, stream, steps, md_steps):
+    """Seconds for `steps` timed steps, from CUDA events on the context's stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.run(md_steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def cpu_baseline_sample(target_s=15.0):
+    """The FP64 oracle, as it stands, on one 8000-atom replica of the workload (single thread)."""
+    from oracle import oracle as O
+    from paper_2103_10449_gb300 import inputs as I
+    x, box = I.diamond(NCELL, NCELL, NCELL)
+    v = I.gaussian_velocities(len(x), math.sqrt(O.KB * T_SW / (O.M_SI * O.MVV2E)), 1000)
+    s = O.System(x=x.copy(), v=v, box=box.copy(), r0=x.copy(), k_E=K_E, T=T_SW, tdamp=0.1, seed=1000,
+                 sched=O.SCHED_FL, nsched=NSCHED)
+    s.setup()
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < target_s or n < 2:
+        s.step()
+        n += 1
+    dt = time.perf_counter() - t0
+    return len(x) * n / dt, n, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2103_10449_gb300 import inputs as I
+    O.build()
+    x, box = I.diamond(NCELL, NCELL, NCELL)
+    v = I.gaussian_velocities(len(x), math.sqrt(O.KB * T_SW / (O.M_SI * O.MVV2E)), 1000)
+    s = O.System(x=x.copy(), v=v, box=box.copy(), r0=x.copy(), k_E=K_E, T=T_SW, tdamp=0.1, seed=1000,
+                 sched=O.SCHED_FL, nsched=NSCHED)
+    s.setup()
+    per_step = 2     # oracle MD steps per timed step (bounded sample of the workload)
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            s.step()
+    dt = time.perf_counter() - t0
+    value = len(x) * per_step * args.steps / dt
+    sample = f"{per_step} MD steps of one 8000-atom replica per timed step (O(N^2) FP64 oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.replicas),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nefe", choices=["nefe", "reference"])
+    ap.add_argument("--replicas", type=int, default=128)
+    ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+
+    from paper_2103_10449_gb300 import nefe as N
+    N.load()
+    R = args.replicas
+    stream = torch.cuda.Stream()
+    ctx, natoms = build_context(N, R, N.NEFE_FP32, seed0=1000 + 7919 * rank, stream=stream)
+    lanes, tune_us = ctx.autotune()
+    ctx.set_profiling(True)
+    for _ in range(args.warmup):
+        ctx.run(MD_STEPS)
+    ctx.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    launches0 = ctx.launch_count()
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    wall = time_steps(torch, ctx, stream, args.steps, MD_STEPS)
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    force_us, nsamp = ctx.profile()
+    mean_cnt, max_cnt, nbuild = ctx.list_stats(-1)
+    t = torch.tensor([wall], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    wall = float(t.item())
+    atoms = natoms * R
+    value = world * atoms * MD_STEPS * args.steps / wall
+
+    # roofline of the dominant kernel (force), from its live CUDA-event durations
+    bytes_per_atom = FORCE_FIXED_BYTES + 4.0 * mean_cnt
+    achieved = bytes_per_atom * atoms / (force_us * 1e-6) / 1e9
+    peak, peak_kind = peaks()
+    tr = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None if tr is None else tr * atoms,
+                "kernel": "k_force (SW + springs + Langevin + half kick)",
+                "algorithmic_bytes_per_atom": bytes_per_atom, "force_us_mean": force_us,
+                "peak_kind": f"{peak_kind} hbm_gbs", "lanes_per_atom": lanes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": workload_config(R), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+            "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild}}
+    del ctx
+
+    if not args.no_extras and rank == 0:
+        # e2e through the public API with host buffers: upload state, run, read results
+        ctx, _ = build_context(N, R, N.NEFE_FP32, seed0=1000)
+        ntot = natoms * R
+        xh = torch.empty((ntot, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vh = torch.empty((ntot, 3), dtype=torch.float64, pin_memory=True).numpy()
+        ctx.get_state_all(xh, vh)
+        for _ in range(2):
+            ctx.set_state_all(xh, vh); ctx.run(MD_STEPS); ctx.results_all()
+        e_steps = max(3, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            ctx.set_state_all(xh, vh)
+            ctx.run(MD_STEPS)
+            ctx.results_all()
+        e2e_wall = time.perf_counter() - t0
+        line["e2e"] = {"value": ntot * MD_STEPS * e_steps / e2e_wall, "unit": UNIT,
+                       "h2d_bytes_per_step": 2 * 8 * 3 * ntot,
+                       "d2h_bytes_per_step": R * 8 * 32,
+                       "path": "nefe_set_state_all (pinned host x, v) + nefe_run + nefe_get_results_all"}
+        del ctx
+        # comparators on the same GPU: plain FP64 single replica, FP32 single replica, FP64 batched
+        comp = {}
+        for name, reps, prec, steps in (("fp64_single_replica", 1, N.NEFE_FP64, 20),
+                                        ("fp32_single_replica", 1, N.NEFE_FP32, 20),
+                                        ("fp64_batched", R, N.NEFE_FP64, 3)):
+            s2 = torch.cuda.Stream()
+            c2, na = build_context(N, reps, prec, stream=s2)
+            for _ in range(2):
+                c2.run(MD_STEPS)
+            c2.sync()
+            w = time_steps(torch, c2, s2, steps, MD_STEPS)
+            comp[name] = na * reps * MD_STEPS * steps / w
+            del c2
+        comp["batched_fp32_over_fp64_single"] = value / world / comp["fp64_single_replica"]
+        comp["batched_fp32_over_fp64_batched"] = value / world / comp["fp64_batched"]
+        line["comparators"] = comp
+        cps, nst, dt = cpu_baseline_sample()
+        line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{nst} FP64-oracle MD steps of one 8000-atom replica ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,105 @@
+// Internal layout of libnefe: device-side descriptors shared by the kernels and the host
+// engine.  Plain structs only (no CUDA types), so host code includes it freely.
+#pragma once
+#include <stdint.h>
+
+namespace nefe {
+
+// Metal units.  kB and hbar are CODATA 2018; MVV2E converts (g/mol) A^2/ps^2 to eV.
+constexpr double kB = 8.617333262e-5;
+constexpr double kMvv2e = 1.66053906660e-23 / 1.602176634e-19;
+constexpr double kEvA3ToGPa = 160.21766340;   // 1 eV/A^3 in GPa (1.602176634e-19 J / 1e-30 m^3)
+
+constexpr int kTile = 128;        // atoms per tile; a tile never straddles two systems
+constexpr int kShell = 32;        // max neighbours inside a*sigma held per atom
+constexpr int kMaxCap = 255;      // max neighbour row capacity
+constexpr int kCodeShift = 27;    // nbr entry = j | (cell-offset code << 27)
+constexpr uint32_t kIndexMask = (1u << kCodeShift) - 1u;
+
+// Fixed-point accumulators: per-system sums are accumulated as int64 in units of 2^-32,
+// so the order in which blocks add them does not change the result (bitwise determinism).
+constexpr double kFix = 4294967296.0;
+enum Acc {
+    ACC_UINT = 0,       // U_int (unscaled SW, or Einstein test potential)
+    ACC_UREF,           // U_E (FL reference)
+    ACC_VIR,            // 6: SW virial xx yy zz xy xz yz (unscaled)
+    ACC_KT = ACC_VIR + 6,   // 6: sum m v_a v_b (eV)
+    ACC_XI = ACC_KT + 6,    // 3: sum of thermostat normals of the current step
+    ACC_N = ACC_XI + 3
+};
+
+enum Sched { SCHED_NONE = 0, SCHED_FL = 1, SCHED_RS = 2, SCHED_AS = 3 };
+enum Pot { POT_SW = 0, POT_EINSTEIN = 1 };
+enum Baro { BARO_NONE = 0, BARO_ISO = 1, BARO_ANISO = 2 };
+
+// Potential constants in the precision of the force kernel.
+template <typename T>
+struct SWc {
+    T inv_sig;     // 1/sigma
+    T a;           // cutoff in sigma units
+    T rc2;         // (a sigma)^2
+    T epsA;        // eps * A
+    T B, p, q;
+    T epslam;      // eps * lambda3
+    T gam;
+    T c0;
+    int int_pq;    // 1 when p == 4 and q == 0 (the standard set): s^-p by multiplications
+};
+
+// Per-system description (constant during a run).
+struct DevSys {
+    int off, n;                 // first atom, atom count
+    int tile0, ntile;           // first tile, tile count
+    int cell0, ncell_cap;       // first cell slot, cell capacity (cell_start uses +1 per system)
+    int pot, sched, direction, baro;
+    long long nsched;
+    double k_int, k_E, lam_f, p_phys, p0, p1, lam0;   // pressures in eV/A^3
+    double mass_e;              // mass * MVV2E (eV ps^2 / A^2)
+    double T, tdamp;
+    unsigned long long seed;
+    int rng_id;                 // system index fed to the noise counter
+    int pair;                   // dCCI pair index or -1
+    double p_ext, pdamp;        // barostat target for SCHED_NONE (eV/A^3), damping (ps)
+    double rcs, skin;           // list radius and skin (A)
+    int trace_every;
+    long long trace_cap, trace_off;
+    int prm;                    // index into the parameter tables
+};
+
+// Per-system dynamic state.
+struct DevState {
+    double box[3];
+    double h[3];                // cell edge at the current box: box / ncell
+    double hb[3];               // cell edge at the last list build
+    int ncell[3];
+    int rebuild;                // set by any atom that moved too far; cleared each step
+    double eta[3];              // barostat strain rates (1/ps)
+    double lam, W, p_tgt;
+    long long k;                // steps completed
+    double u_int, u_ref, vir[6], kt[6];
+    double sums[5];             // running sums: H, dH/dl, P, V, count
+    double s[3], phi[3];        // drift factors for the current step
+    double scale_int, scale_E;  // force scales at the current lambda
+    double thr2;                // squared displacement that triggers a rebuild
+    double dHdl, H, V, P[6];    // last observation
+    unsigned err;
+    int pad;
+    long long trace_n;
+    long long nbuild;           // list builds so far
+};
+
+struct DevPair {
+    int a, b, mode, pad;
+    double T0, frm, to;         // TEMP: K; PRESS: eV/A^3
+    long long nsteps, k;
+    double lam, ps;             // current lambda and scaled pressure (eV/A^3)
+    unsigned err;
+    int pad2;
+};
+
+// One group per independent update unit: a single system (b = -1) or a dCCI pair.
+struct DevGroup {
+    int a, b, pair, pad;
+};
+
+}  // namespace nefe

@@ -1,0 +1,70 @@
+// Host-side launchers of the libnefe kernels (defined in nefe_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "nefe_dev.h"
+
+namespace nefe {
+
+constexpr int kSlots = 32;   // accumulator slots per system (spreads atomics over 32 words)
+
+// Pointers handed to every kernel.  Per-atom arrays are global over all systems of a
+// context; FP64 SoA arrays have stride ntot.  F/xs/xsb are float4 (FP32 path) or double4.
+struct Bufs {
+    const DevSys* sys;
+    DevState* st;
+    long long* acc;          // [nsys][ACC_N][kSlots]
+    const int* tile_sys;     // system of each 128-atom tile
+    double* x;
+    double* v;
+    const double* r0;
+    void* F;                 // total force used by the next half kick
+    void* xs;                // mirror: x - q h, FP32 or FP64
+    void* xsb;               // mirror at the last list build
+    int4* q;                 // unwrapped cell index per axis, from the last build
+    int* cell_of;
+    int* perm;
+    int* cell_start;         // per system: ncell_cap + 1 entries at cell0 + system index
+    int* cell_count;
+    int* cell_cursor;
+    int* nbr;
+    int* cnt;
+    int cap;
+    int ntot;
+    double dt;
+    const void* swc;         // SWc<float> or SWc<double> table
+    DevPair* pairs;
+    double* trace;
+    double* f_out;           // stateless: FP64 SoA forces
+    double* e_atom;          // stateless: per-atom energy (may be NULL)
+};
+
+enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };
+
+// Cell count / scan / fill / sort only (the stateless cell sort).
+void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
+                  cudaStream_t s, long* launches);
+// Decodes one system's fixed-point sums into [U_int, virial xx yy zz xy xz yz] (FP64, device).
+void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s);
+// Rebuild sequence (only systems whose rebuild flag is set, or all when force_all).
+void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
+                           cudaStream_t s, long* launches);
+// Half kick + drift + mirror + displacement check + noise sums (mode 0: no kick/drift).
+void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s,
+                       long* launches);
+// SW (+ springs, + Langevin and second half kick in FM_SETUP / FM_STEP).
+void launch_force(const Bufs& b, int precision, int lanes, int ntiles, int mode,
+                  cudaStream_t s, long* launches);
+// Per-group scalar update. mode 0 INIT, 1 STEP, 2 OBSERVE.
+void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,
+                  long* launches);
+// Mirror only (stateless force entry): q and xs from x with the list-build formula.
+void launch_mirror(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches);
+// Thermostat noise as FP64 (n,3).
+void launch_noise(unsigned long long seed, unsigned long long sys_id, unsigned long long step,
+                  int n, int precision, double* xi, cudaStream_t s);
+
+bool lanes_supported(int lanes);
+// (n,3) row-major <-> SoA (to_soa = 1: aos -> soa).
+void launch_aos_soa(const double* src, double* dst, int n, int to_soa, cudaStream_t s);
+
+}  // namespace nefe

@@ -1,0 +1,356 @@
+"""ctypes binding of libnefe.so (include/nefe.h): same names, argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels.  Device buffers passed
+to the stateless calls are torch CUDA tensors (their data pointers are handed over);
+PyTorch only provides device memory and streams.  Importing this module does not need a
+GPU; calling into the library does, and a missing library raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NEFE_OK, NEFE_EINVAL, NEFE_ENOMEM, NEFE_ECUDA, NEFE_EOVERFLOW = 0, -1, -2, -3, -4
+NEFE_ENAN, NEFE_EDEGEN, NEFE_ETIMEOUT, NEFE_ESTATE = -6, -7, -8, -9
+NEFE_ERR_NBR_OVERFLOW, NEFE_ERR_SHELL_OVERFLOW, NEFE_ERR_NAN, NEFE_ERR_DEGEN, NEFE_ERR_BOX = 1, 2, 4, 8, 16
+NEFE_FP32, NEFE_FP64 = 0, 1
+NEFE_POT_SW, NEFE_POT_EINSTEIN = 0, 1
+NEFE_BARO_NONE, NEFE_BARO_ISO, NEFE_BARO_ANISO = 0, 1, 2
+NEFE_SCHED_NONE, NEFE_SCHED_FL, NEFE_SCHED_RS, NEFE_SCHED_AS = 0, 1, 2, 3
+NEFE_DCCI_TEMP, NEFE_DCCI_PRESS = 0, 1
+CODE_SHIFT = 27
+INDEX_MASK = (1 << CODE_SHIFT) - 1
+
+
+class NefeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libnefe error {code}: {msg}")
+        self.code = code
+
+
+class nefe_sw_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("eps", "sigma", "A", "B", "p", "q", "a", "lambda3",
+                                               "gamma", "cos0")]
+
+
+class nefe_system_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("x", ctypes.POINTER(ctypes.c_double)),
+                ("v", ctypes.POINTER(ctypes.c_double)), ("r0", ctypes.POINTER(ctypes.c_double)),
+                ("box", ctypes.c_double * 3), ("mass", ctypes.c_double), ("pot", ctypes.c_int),
+                ("k_int", ctypes.c_double)]
+
+
+class nefe_schedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("direction", ctypes.c_int), ("nsteps", ctypes.c_long),
+                ("k_E", ctypes.c_double), ("lambda_f", ctypes.c_double), ("P_GPa", ctypes.c_double),
+                ("P0_GPa", ctypes.c_double), ("P1_GPa", ctypes.c_double), ("lambda0", ctypes.c_double)]
+
+
+class nefe_results(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_double), ("lambda_", ctypes.c_double), ("step", ctypes.c_long),
+                ("U", ctypes.c_double), ("U_E", ctypes.c_double), ("K", ctypes.c_double),
+                ("T", ctypes.c_double), ("P", ctypes.c_double * 6), ("V", ctypes.c_double),
+                ("box", ctypes.c_double * 3), ("dHdl", ctypes.c_double), ("H", ctypes.c_double),
+                ("mean_H", ctypes.c_double), ("mean_dHdl", ctypes.c_double),
+                ("mean_P", ctypes.c_double), ("mean_V", ctypes.c_double),
+                ("P_target", ctypes.c_double), ("error", ctypes.c_uint)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if isinstance(v, ctypes.Array):
+                v = np.array(v[:])
+            d[name.rstrip("_")] = v
+        return d
+
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+# name -> (argtypes); every function returns int except nefe_last_error
+SIGNATURES = {
+    "nefe_sw_params_silicon": [ctypes.POINTER(nefe_sw_params)],
+    "nefe_cell_bin": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _c_int_p, _vp, _vp, _vp, ctypes.c_int, _vp],
+    "nefe_neighbor_build": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, ctypes.c_int, _vp, _vp, _c_int_p, _vp],
+    "nefe_sw_forces": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
+                       ctypes.POINTER(nefe_sw_params), ctypes.c_int, _vp, _vp, _vp, _c_int_p, _vp],
+    "nefe_langevin_noise": [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _vp, _vp],
+    "nefe_create": [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int],
+    "nefe_destroy": [_vp],
+    "nefe_add_system": [_vp, ctypes.POINTER(nefe_system_desc), _c_int_p],
+    "nefe_set_sw_params": [_vp, ctypes.c_int, ctypes.POINTER(nefe_sw_params)],
+    "nefe_set_thermostat": [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64],
+    "nefe_set_barostat": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double],
+    "nefe_set_schedule": [_vp, ctypes.c_int, ctypes.POINTER(nefe_schedule)],
+    "nefe_pair_dcci": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                       ctypes.c_double, ctypes.c_double, ctypes.c_long, _c_int_p],
+    "nefe_set_trace": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_long],
+    "nefe_setup": [_vp],
+    "nefe_run": [_vp, ctypes.c_long],
+    "nefe_sync": [_vp],
+    "nefe_get_results": [_vp, ctypes.c_int, ctypes.POINTER(nefe_results)],
+    "nefe_get_pair": [_vp, ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.POINTER(ctypes.c_uint)],
+    "nefe_get_state": [_vp, ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "nefe_set_state": [_vp, ctypes.c_int, _c_dbl_p, _c_dbl_p],
+    "nefe_get_trace": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_long, ctypes.POINTER(ctypes.c_long)],
+    "nefe_save": [_vp, ctypes.c_char_p],
+    "nefe_load": [_vp, ctypes.c_char_p],
+    "nefe_autotune": [_vp],
+    "nefe_get_tuning": [_vp, _c_int_p, _c_dbl_p],
+    "nefe_set_tuning": [_vp, ctypes.c_int],
+    "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
+    "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
+    "nefe_get_state_all": [_vp, _c_dbl_p, _c_dbl_p],
+    "nefe_get_results_all": [_vp, ctypes.POINTER(nefe_results), ctypes.c_int],
+    "nefe_get_list_stats": [_vp, ctypes.c_int, _c_dbl_p, _c_int_p, ctypes.POINTER(ctypes.c_long)],
+    "nefe_set_profiling": [_vp, ctypes.c_int],
+    "nefe_get_profile": [_vp, _c_dbl_p, ctypes.POINTER(ctypes.c_long)],
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libnefe.so (building it with nvcc first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise NefeError(NEFE_ECUDA, f"{path} is missing: run paper_2103_10449_gb300.build")
+    L = ctypes.CDLL(path)
+    for name, argtypes in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.argtypes = argtypes
+        fn.restype = ctypes.c_int
+    L.nefe_last_error.argtypes = []
+    L.nefe_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != NEFE_OK:
+        raise NefeError(rc, load().nefe_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _box(box):
+    return (ctypes.c_double * 3)(*[float(b) for b in box])
+
+
+def nefe_sw_params_silicon() -> nefe_sw_params:
+    p = nefe_sw_params()
+    _check(load().nefe_sw_params_silicon(ctypes.byref(p)))
+    return p
+
+
+def params_from(seq) -> nefe_sw_params:
+    return nefe_sw_params(*[float(v) for v in seq])
+
+
+# ---------------------------------------------------------------------- stateless calls
+def nefe_cell_bin(x, n, box, rcs, cell_of, cell_start, perm, ncell_cap, stream=None):
+    nc3 = (ctypes.c_int * 3)()
+    _check(load().nefe_cell_bin(_ptr(x), int(n), _box(box), float(rcs), nc3, _ptr(cell_of),
+                                _ptr(cell_start), _ptr(perm), int(ncell_cap), _stream(stream)))
+    return tuple(nc3)
+
+
+def nefe_neighbor_build(x, n, box, rcs, cap, nbr, cnt, stream=None, check=True):
+    ovf = ctypes.c_int(0)
+    rc = load().nefe_neighbor_build(_ptr(x), int(n), _box(box), float(rcs), int(cap), _ptr(nbr), _ptr(cnt),
+                                    ctypes.byref(ovf), _stream(stream))
+    if check or rc not in (NEFE_OK, NEFE_EOVERFLOW):
+        _check(rc)
+    return ovf.value
+
+
+def nefe_sw_forces(x, n, box, rcs, nbr, cnt, cap, prm, precision, f, e_atom=None, energy_virial=None,
+                   stream=None):
+    ovf = ctypes.c_int(0)
+    _check(load().nefe_sw_forces(_ptr(x), int(n), _box(box), float(rcs), _ptr(nbr), _ptr(cnt), int(cap),
+                                 ctypes.byref(prm), int(precision), _ptr(f), _ptr(e_atom),
+                                 _ptr(energy_virial), ctypes.byref(ovf), _stream(stream)))
+    return ovf.value
+
+
+def nefe_langevin_noise(seed, sys_id, step, n, precision, xi, stream=None):
+    _check(load().nefe_langevin_noise(int(seed), int(sys_id), int(step), int(n), int(precision), _ptr(xi),
+                                      _stream(stream)))
+
+
+# ---------------------------------------------------------------------- context API
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_c_dbl_p)
+
+
+class Context:
+    """Owns one nefe_ctx; methods are the nefe_* context calls with numpy arguments."""
+
+    def __init__(self, device=0, precision=NEFE_FP32, dt=0.001, skin=0.5, nbr_cap=48, stream=None):
+        self._L = load()
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(self._L.nefe_create(ctypes.byref(h), int(device), s, int(precision), float(dt), float(skin),
+                                   int(nbr_cap)))
+        self.h = h
+        self.n = []
+        self._keep = []
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self._L.nefe_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_system(self, x, box, v=None, r0=None, mass=28.0855, pot=NEFE_POT_SW, k_int=0.0):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        r0 = None if r0 is None else np.ascontiguousarray(r0, dtype=np.float64)
+        d = nefe_system_desc(n=x.shape[0], x=_dp(x), v=_dp(v), r0=_dp(r0),
+                             box=(ctypes.c_double * 3)(*[float(b) for b in box]), mass=float(mass),
+                             pot=int(pot), k_int=float(k_int))
+        sid = ctypes.c_int(-1)
+        _check(self._L.nefe_add_system(self.h, ctypes.byref(d), ctypes.byref(sid)))
+        self.n.append(x.shape[0])
+        return sid.value
+
+    def set_sw_params(self, sys, prm):
+        _check(self._L.nefe_set_sw_params(self.h, int(sys), ctypes.byref(prm)))
+
+    def set_thermostat(self, sys, T, damp, seed):
+        _check(self._L.nefe_set_thermostat(self.h, int(sys), float(T), float(damp), int(seed)))
+
+    def set_barostat(self, sys, mode, P_GPa, pdamp):
+        _check(self._L.nefe_set_barostat(self.h, int(sys), int(mode), float(P_GPa), float(pdamp)))
+
+    def set_schedule(self, sys, kind, direction=1, nsteps=1, k_E=0.0, lambda_f=1.0, P_GPa=0.0, P0_GPa=0.0,
+                     P1_GPa=0.0, lambda0=1.0):
+        s = nefe_schedule(kind=kind, direction=direction, nsteps=nsteps, k_E=k_E, lambda_f=lambda_f, P_GPa=P_GPa,
+                          P0_GPa=P0_GPa, P1_GPa=P1_GPa, lambda0=lambda0)
+        _check(self._L.nefe_set_schedule(self.h, int(sys), ctypes.byref(s)))
+
+    def pair_dcci(self, a, b, T0, P0_GPa, mode, frm, to, nsteps):
+        pid = ctypes.c_int(-1)
+        _check(self._L.nefe_pair_dcci(self.h, int(a), int(b), float(T0), float(P0_GPa), int(mode), float(frm),
+                                      float(to), int(nsteps), ctypes.byref(pid)))
+        return pid.value
+
+    def set_trace(self, sys, every, cap):
+        _check(self._L.nefe_set_trace(self.h, int(sys), int(every), int(cap)))
+
+    def setup(self):
+        _check(self._L.nefe_setup(self.h))
+
+    def run(self, nsteps):
+        _check(self._L.nefe_run(self.h, int(nsteps)))
+
+    def sync(self):
+        _check(self._L.nefe_sync(self.h))
+
+    def results(self, sys):
+        r = nefe_results()
+        _check(self._L.nefe_get_results(self.h, int(sys), ctypes.byref(r)))
+        return r.as_dict()
+
+    def pair(self, p):
+        T, P, lam, err = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_uint()
+        _check(self._L.nefe_get_pair(self.h, int(p), ctypes.byref(T), ctypes.byref(P), ctypes.byref(lam),
+                                     ctypes.byref(err)))
+        return T.value, P.value, lam.value, err.value
+
+    def get_state(self, sys):
+        n = self.n[sys]
+        x = np.zeros((n, 3)); v = np.zeros((n, 3)); box = np.zeros(3)
+        _check(self._L.nefe_get_state(self.h, int(sys), _dp(x), _dp(v), _dp(box)))
+        return x, v, box
+
+    def set_state(self, sys, x=None, v=None):
+        x = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        _check(self._L.nefe_set_state(self.h, int(sys), _dp(x), _dp(v)))
+
+    def trace(self, sys, cap=1 << 20):
+        buf = np.zeros((cap, 9))
+        n = ctypes.c_long(0)
+        _check(self._L.nefe_get_trace(self.h, int(sys), _dp(buf), int(cap), ctypes.byref(n)))
+        return buf[: n.value].copy()
+
+    def save(self, path):
+        _check(self._L.nefe_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        _check(self._L.nefe_load(self.h, str(path).encode()))
+
+    def autotune(self):
+        _check(self._L.nefe_autotune(self.h))
+        return self.tuning()
+
+    def tuning(self):
+        lanes, us = ctypes.c_int(), ctypes.c_double()
+        _check(self._L.nefe_get_tuning(self.h, ctypes.byref(lanes), ctypes.byref(us)))
+        return lanes.value, us.value
+
+    def set_tuning(self, lanes):
+        _check(self._L.nefe_set_tuning(self.h, int(lanes)))
+
+    def set_state_all(self, x=None, v=None):
+        """x, v: host (Ntot, 3) float64 arrays (pinned memory makes the copy faster)."""
+        _check(self._L.nefe_set_state_all(self.h, _dp(x), _dp(v)))
+
+    def get_state_all(self, x=None, v=None):
+        _check(self._L.nefe_get_state_all(self.h, _dp(x), _dp(v)))
+
+    def results_all(self, count=None):
+        count = len(self.n) if count is None else count
+        arr = (nefe_results * max(1, count))()
+        _check(self._L.nefe_get_results_all(self.h, arr, int(count)))
+        return [arr[i].as_dict() for i in range(count)]
+
+    def list_stats(self, sys=-1):
+        m, mx, nb = ctypes.c_double(), ctypes.c_int(), ctypes.c_long()
+        _check(self._L.nefe_get_list_stats(self.h, int(sys), ctypes.byref(m), ctypes.byref(mx), ctypes.byref(nb)))
+        return m.value, mx.value, nb.value
+
+    def set_profiling(self, enable=True):
+        _check(self._L.nefe_set_profiling(self.h, int(bool(enable))))
+
+    def profile(self):
+        us, n = ctypes.c_double(), ctypes.c_long()
+        _check(self._L.nefe_get_profile(self.h, ctypes.byref(us), ctypes.byref(n)))
+        return us.value, n.value
+
+    def launch_count(self):
+        c = ctypes.c_long(0)
+        _check(self._L.nefe_launch_count(self.h, ctypes.byref(c)))
+        return c.value

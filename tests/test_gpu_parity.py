@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances: neighbour lists and cells bit-exact; SW energy,
+forces and virial within 1e-10 (FP64 kernel) or 1e-5 (FP32 kernel) relative, forces measured
+normwise as max|dF| / max|F|; thermostat noise bit-exact in its integer stream and within
+1e-14 (FP64 transform) / 2e-6 (FP32 transform).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2103_10449_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RC = O.SW_SI[6] * O.SW_SI[1]
+SKIN = 0.5
+RCS = RC + SKIN
+CAP = 48
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2103_10449_gb300 import nefe
+    nefe.load()
+    return nefe
+
+
+def soa(x):
+    return torch.tensor(np.ascontiguousarray(x.T).reshape(-1), dtype=torch.float64, device="cuda")
+
+
+def configs():
+    out = {}
+    x, b = I.diamond(2, 2, 2)
+    out["diamond64"] = (I.rattle(x, 0.1, 1), b)                 # 2 cells per axis
+    x, b = I.diamond(5, 5, 5)
+    out["diamond1000"] = (I.rattle(x, 0.15, 2), b)              # 7 tiles + ragged 104
+    x, b = I.beta_tin(6, 6, 12)
+    out["betatin1728"] = (I.rattle(x, 0.1, 3), b)
+    x, b = I.liquid(1500, 0.05425, seed=4)
+    out["liquid1500"] = (x + np.array([60.0, -30.0, 0.5]), b)   # unwrapped coordinates
+    return out
+
+
+CONFIGS = configs()
+
+
+def gpu_list(N, x, box, cap=CAP):
+    n = len(x)
+    xd = soa(x)
+    nbr = torch.zeros(n * cap, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    N.nefe_neighbor_build(xd, n, box, RCS, cap, nbr, cnt)
+    torch.cuda.synchronize()
+    return xd, nbr, cnt
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_cell_bin_bit_exact(N, name):
+    x, box = CONFIGS[name]
+    n = len(x)
+    nc_o, cell_o, start_o, perm_o = O.cell_bin(x, box, RCS)
+    xd = soa(x)
+    cap = int(np.prod(nc_o))
+    cell = torch.zeros(n, dtype=torch.int32, device="cuda")
+    start = torch.zeros(cap + 1, dtype=torch.int32, device="cuda")
+    perm = torch.zeros(n, dtype=torch.int32, device="cuda")
+    nc = N.nefe_cell_bin(xd, n, box, RCS, cell, start, perm, cap)
+    torch.cuda.synchronize()
+    assert tuple(nc) == tuple(nc_o)
+    assert np.array_equal(cell.cpu().numpy(), cell_o)
+    assert np.array_equal(start.cpu().numpy(), start_o)
+    assert np.array_equal(perm.cpu().numpy(), perm_o)
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_neighbor_list_bit_exact(N, name):
+    x, box = CONFIGS[name]
+    n = len(x)
+    nbr_o, cnt_o, img_o = O.neighbor_list(x, box, RCS, cap=CAP)
+    _, nbr, cnt = gpu_list(N, x, box)
+    nbr = nbr.cpu().numpy().reshape(n, CAP)
+    cnt = cnt.cpu().numpy()
+    assert np.array_equal(cnt, cnt_o)
+    for i in range(n):
+        j = nbr[i, :cnt[i]] & N.INDEX_MASK
+        assert np.array_equal(j, nbr_o[i, :cnt[i]])
+    # the stored cell offsets reproduce the minimum-image displacement
+    code = (nbr >> N.CODE_SHIFT) & 31
+    o = np.stack([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], axis=-1)
+    nc = np.array([int(np.floor(box[k] / RCS)) for k in range(3)])
+    for k in range(3):
+        while box[k] / nc[k] < RCS * (1 + 1e-9):
+            nc[k] -= 1
+    h = box / nc
+    s = x / box
+    fl = np.floor(s)
+    c = np.minimum(((s - fl) * nc).astype(int), nc - 1)
+    q = fl.astype(int) * nc + c
+    xs = x - q * h
+    for i in range(0, n, max(1, n // 50)):
+        jj = nbr[i, :cnt[i]] & N.INDEX_MASK
+        d = xs[jj] - xs[i] + o[i, :cnt[i]] * h
+        d_o = x[nbr_o[i, :cnt[i]]] - x[i] - img_o[i, :cnt[i]] * box
+        assert np.abs(d - d_o).max() < 1e-9
+
+
+def _forces(N, x, box, precision):
+    n = len(x)
+    xd, nbr, cnt = gpu_list(N, x, box)
+    f = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    ea = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ev = torch.zeros(7, dtype=torch.float64, device="cuda")
+    prm = N.params_from(O.SW_SI)
+    N.nefe_sw_forces(xd, n, box, RCS, nbr, cnt, CAP, prm, precision, f, ea, ev)
+    torch.cuda.synchronize()
+    return f.cpu().numpy().reshape(3, n).T, ea.cpu().numpy(), ev.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-5)])
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_sw_energy_forces_virial(N, name, precision, tol):
+    x, box = CONFIGS[name]
+    e_o, f_o, vir_o, ea_o = O.sw_energy(x, box)
+    f, ea, ev = _forces(N, x, box, precision)
+    fscale = np.abs(f_o).max()
+    assert np.abs(f - f_o).max() <= tol * fscale
+    assert abs(ev[0] - e_o) <= tol * abs(e_o)
+    assert np.abs(ea - ea_o).max() <= tol * np.abs(ea_o).max()
+    vscale = np.abs(vir_o).max()
+    assert np.abs(ev[1:] - vir_o).max() <= tol * vscale * 10
+
+
+def test_sw_forces_deterministic(N):
+    x, box = CONFIGS["liquid1500"]
+    a = _forces(N, x, box, 0)
+    b = _forces(N, x, box, 0)
+    assert all(np.array_equal(u, v) for u, v in zip(a, b))
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-14), (0, 2e-6)])
+def test_langevin_noise(N, precision, tol):
+    n = 5000
+    xi = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    N.nefe_langevin_noise(17, 3, 12345, n, precision, xi)
+    torch.cuda.synchronize()
+    got = xi.cpu().numpy().reshape(n, 3)
+    ref = O.langevin_xi(17, 3, 12345, n)
+    assert np.abs(got - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+def test_neighbor_overflow_and_bad_box_are_errors(N):
+    x, box = CONFIGS["liquid1500"]
+    n = len(x)
+    xd = soa(x)
+    nbr = torch.zeros(n * 8, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ovf = N.nefe_neighbor_build(xd, n, box, RCS, 8, nbr, cnt, check=False)
+    assert ovf == 1
+    with pytest.raises(N.NefeError):
+        N.nefe_neighbor_build(xd, n, np.array([8.0, 8.0, 8.0]), RCS, CAP, nbr, cnt)
+    # empty input is a no-op
+    N.nefe_neighbor_build(xd, 0, box, RCS, CAP, nbr, cnt)
+
+
+# ------------------------------------------------------------------ trajectories
+def _sv(T):
+    return math.sqrt(O.KB * T / (O.M_SI * O.MVV2E))
+
+
+def _fl_pair(precision, nsteps=300, T=400.0):
+    x0, box = I.diamond(2, 2, 2)
+    v0 = I.gaussian_velocities(len(x0), _sv(T), 1)
+    orc = O.System(x=x0.copy(), v=v0.copy(), box=box.copy(), r0=x0.copy(), k_E=5.0, T=T, tdamp=0.1,
+                   seed=9, sys_id=0, sched=O.SCHED_FL, direction=1, nsched=1000, trace_every=0)
+    orc.run(nsteps)
+    from paper_2103_10449_gb300 import nefe
+    ctx = nefe.Context(precision=precision, skin=SKIN, nbr_cap=CAP)
+    s = ctx.add_system(x0, box, v=v0, r0=x0)
+    ctx.set_thermostat(s, T, 0.1, 9)
+    ctx.set_schedule(s, nefe.NEFE_SCHED_FL, direction=1, nsteps=1000, k_E=5.0)
+    ctx.run(nsteps)
+    res = ctx.results(s)
+    x, v, _ = ctx.get_state(s)
+    ctx.close()
+    return orc, res, x, v
+
+
+def test_frenkel_ladd_trajectory_fp64_matches_oracle(N):
+    orc, res, x, v = _fl_pair(1)
+    ro = orc.results()
+    assert res["step"] == ro["step"] == 300
+    assert np.abs(x - orc.x).max() < 1e-8
+    assert np.abs(v - orc.v).max() < 1e-6
+    assert res["W"] == pytest.approx(ro["W"], rel=1e-8, abs=1e-9)
+    assert res["lambda"] == pytest.approx(ro["lam"], rel=1e-14)
+    assert res["U"] == pytest.approx(ro["U"], rel=1e-9)
+    assert res["U_E"] == pytest.approx(ro["U_E"], rel=1e-7, abs=1e-9)
+    assert res["T"] == pytest.approx(ro["T"], rel=1e-7)
+
+
+def test_frenkel_ladd_trajectory_fp32_close_to_oracle(N):
+    orc, res, x, v = _fl_pair(0, nsteps=100)
+    ro = orc.results()
+    assert np.abs(x - orc.x).max() < 1e-4
+    assert res["W"] == pytest.approx(ro["W"], rel=1e-3, abs=1e-3)
+    assert res["U"] == pytest.approx(ro["U"], rel=1e-5)
+
+
+def test_run_is_bitwise_deterministic(N):
+    a = _fl_pair(0, nsteps=200)
+    b = _fl_pair(0, nsteps=200)
+    assert a[1]["W"] == b[1]["W"] and np.array_equal(a[2], b[2])
