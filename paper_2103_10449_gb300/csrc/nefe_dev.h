@@ -61,6 +61,9 @@ struct DevSys {
     int pair;                   // dCCI pair index or -1
     double p_ext, pdamp;        // barostat target for SCHED_NONE (eV/A^3), damping (ps)
     double rcs, skin;           // list radius and skin (A)
+    double amp;                 // Langevin noise amplitude sqrt(2 m kB T / (tdamp dt)) (eV/A)
+    double gam;                 // Langevin friction m / tdamp (eV ps / A^2)
+    double ckick;               // dt / (2 m) (A^2 / (eV ps))
     int trace_every;
     long long trace_cap, trace_off;
     int prm;                    // index into the parameter tables

@@ -217,6 +217,9 @@ int setup(nefe_ctx* c) {
         d.pdamp = h.pdamp;
         d.rcs = rcs;
         d.skin = c->skin;
+        d.amp = h.tdamp > 0.0 ? std::sqrt(2.0 * d.mass_e * kB * h.T / (h.tdamp * c->dt)) : 0.0;
+        d.gam = h.tdamp > 0.0 ? d.mass_e / h.tdamp : 0.0;
+        d.ckick = 0.5 * c->dt / d.mass_e;
         d.trace_every = h.trace_every;
         d.trace_cap = h.trace_cap;
         d.trace_off = tr;

@@ -82,17 +82,17 @@ template <> struct Noise<float> {
 // Deterministic per-system sums: warp shuffle -> shared -> one int64 fixed-point atomic per
 // value into slot (blockIdx % kSlots).  Every thread of the block must call it.
 // ------------------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void block_sum_to_acc(double (&v)[K], long long* acc_sys, int first,
+template <typename T, int K>
+__device__ __forceinline__ void block_sum_to_acc(T (&v)[K], long long* acc_sys, int first,
                                                  unsigned* err) {
     __shared__ double red[kTile / 32][K];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double x = v[k];
+        T x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[w][k] = x;
+        if (lane == 0) red[w][k] = (double)x;
     }
     __syncthreads();
     if (threadIdx.x < K) {
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
     const TileAtom ta = tile_of(b, blockIdx.x);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
-    double xs_sum[3] = {0.0, 0.0, 0.0};
+    T xs_sum[3] = {(T)0, (T)0, (T)0};
     if ((int)threadIdx.x < ta.count) {
         const int i = ta.first + threadIdx.x;
         const size_t N = b.ntot;
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
             xs_sum[0] = z[0]; xs_sum[1] = z[1]; xs_sum[2] = z[2];
         }
     }
-    block_sum_to_acc<3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &st.err);
+    block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &st.err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -468,6 +468,15 @@ __global__ void __launch_bounds__(kTile) k_force(Bufs b) {
     const int ia = part * G + grp;
     const bool valid = ia < ta.count;
     const int i = ta.first + ia;
+    // per-system mean of this step's thermostat noise (sum of the 32 slots, once per block)
+    __shared__ T s_xm[3];
+    if (MODE != FM_FORCES && threadIdx.x < 3) {
+        const long long* acc = b.acc + (size_t)ta.sys * ACC_N * kSlots + (size_t)(ACC_XI + threadIdx.x) * kSlots;
+        long long sum = 0;
+        for (int sl = 0; sl < kSlots; ++sl) sum += acc[sl];
+        s_xm[threadIdx.x] = (T)((double)sum / kFix / (double)S.n);
+    }
+    __syncthreads();
 
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
@@ -608,65 +617,61 @@ __global__ void __launch_bounds__(kTile) k_force(Bufs b) {
     }
     if (shell_ovf && lane == 0) atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
 
-    double red[14];
+    T red[14];
 #pragma unroll
-    for (int k = 0; k < 14; ++k) red[k] = 0.0;
+    for (int k = 0; k < 14; ++k) red[k] = (T)0;
     if (valid && lane == 0) {
         const size_t N = b.ntot;
-        double fint[3] = {(double)fx, (double)fy, (double)fz};
-        double u_int = (double)en, u_ref = 0.0;
-        double fe[3] = {0.0, 0.0, 0.0};
+        T fint[3] = {fx, fy, fz};
+        T u_int = en, u_ref = 0;
+        T fe[3] = {(T)0, (T)0, (T)0};
         if (MODE == FM_FORCES) {
-            b.f_out[i] = fint[0]; b.f_out[N + i] = fint[1]; b.f_out[2 * N + i] = fint[2];
-            if (b.e_atom) b.e_atom[i] = u_int;
+            b.f_out[i] = (double)fint[0]; b.f_out[N + i] = (double)fint[1]; b.f_out[2 * N + i] = (double)fint[2];
+            if (b.e_atom) b.e_atom[i] = (double)u_int;
         } else {
             if (S.pot == POT_EINSTEIN || S.k_E > 0.0) {
+                // spring displacement from FP64 positions; energies in FP64
                 double d[3];
                 for (int k = 0; k < 3; ++k) d[k] = b.x[k * N + i] - b.r0[k * N + i];
                 const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                 if (S.pot == POT_EINSTEIN) {
-                    u_int = 0.5 * S.k_int * d2;
-                    for (int k = 0; k < 3; ++k) fint[k] = -S.k_int * d[k];
+                    u_int = (T)(0.5 * S.k_int * d2);
+                    for (int k = 0; k < 3; ++k) fint[k] = (T)(-S.k_int) * (T)d[k];
                 }
                 if (S.k_E > 0.0) {
-                    u_ref = 0.5 * S.k_E * d2;
-                    for (int k = 0; k < 3; ++k) fe[k] = -S.k_E * d[k];
+                    u_ref = (T)(0.5 * S.k_E * d2);
+                    for (int k = 0; k < 3; ++k) fe[k] = (T)(-S.k_E) * (T)d[k];
                 }
             }
-            double F[3], v[3] = {b.v[i], b.v[N + i], b.v[2 * N + i]};
-            for (int k = 0; k < 3; ++k) F[k] = st.scale_int * fint[k] + st.scale_E * fe[k];
+            double v[3] = {b.v[i], b.v[N + i], b.v[2 * N + i]};
+            const T si = (T)st.scale_int, se = (T)st.scale_E;
+            T F[3];
+            for (int k = 0; k < 3; ++k) F[k] = si * fint[k] + se * fe[k];
             if (S.tdamp > 0.0) {
-                const long long* acc = b.acc + (size_t)ta.sys * ACC_N * kSlots;
-                double xm[3];
-                for (int k = 0; k < 3; ++k) {
-                    long long sum = 0;
-                    for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)(ACC_XI + k) * kSlots + sl];
-                    xm[k] = (double)sum / kFix / (double)S.n;
-                }
                 T z[3];
                 Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)st.k, (uint64_t)(i - S.off), z);
-                const double amp = sqrt(2.0 * S.mass_e * kB * S.T / (S.tdamp * b.dt));
-                const double gam = S.mass_e / S.tdamp;
-                for (int k = 0; k < 3; ++k) F[k] += -gam * v[k] + amp * ((double)z[k] - xm[k]);
+                const T amp = (T)S.amp, gam = (T)S.gam;
+                for (int k = 0; k < 3; ++k) F[k] += -gam * (T)v[k] + amp * (z[k] - s_xm[k]);
             }
             if (MODE == FM_STEP) {
-                const double c = 0.5 * b.dt / S.mass_e;
-                for (int k = 0; k < 3; ++k) { v[k] += c * F[k]; b.v[k * N + i] = v[k]; }
+                for (int k = 0; k < 3; ++k) { v[k] += S.ckick * (double)F[k]; b.v[k * N + i] = v[k]; }
             }
-            reinterpret_cast<T4*>(b.F)[i] = mk4((T)F[0], (T)F[1], (T)F[2], (T)0);
-            red[8] = S.mass_e * v[0] * v[0];
-            red[9] = S.mass_e * v[1] * v[1];
-            red[10] = S.mass_e * v[2] * v[2];
-            red[11] = S.mass_e * v[0] * v[1];
-            red[12] = S.mass_e * v[0] * v[2];
-            red[13] = S.mass_e * v[1] * v[2];
+            reinterpret_cast<T4*>(b.F)[i] = mk4(F[0], F[1], F[2], (T)0);
+            const T me = (T)S.mass_e;
+            const T vx = (T)v[0], vy = (T)v[1], vz = (T)v[2];
+            red[8] = me * vx * vx;
+            red[9] = me * vy * vy;
+            red[10] = me * vz * vz;
+            red[11] = me * vx * vy;
+            red[12] = me * vx * vz;
+            red[13] = me * vy * vz;
         }
         red[0] = u_int;
         red[1] = u_ref;
-        red[2] = (double)w0; red[3] = (double)w1; red[4] = (double)w2;
-        red[5] = (double)w3; red[6] = (double)w4; red[7] = (double)w5;
+        red[2] = w0; red[3] = w1; red[4] = w2;
+        red[5] = w3; red[6] = w4; red[7] = w5;
     }
-    block_sum_to_acc<14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
 
 // ------------------------------------------------------------------------------------
