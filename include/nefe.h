@@ -104,6 +104,31 @@ NEFE_API int nefe_cell_bin(const double* x, int n, const double box[3], double r
                   void* stream);
 
 /*
+ * nefe_cell_bin_noalloc - the same cell grid, cell ids, occupancy prefix sum and stable sort
+ * as nefe_cell_bin (identical outputs for identical inputs), for callers that cannot allocate
+ * device memory: code running under another framework's memory pool, real-time loops that
+ * must never enter the CUDA allocator, or processes whose device memory is reserved up
+ * front.  It calls no cudaMalloc, cudaFree, cudaMallocAsync or allocating library routine.
+ * (The paper has no counterpart: this is a deployment variant of the cell sort.)
+ *   Arguments and outputs as nefe_cell_bin; the caller still owns x, cell_of, cell_start
+ *   and perm.
+ *   Limits: n <= NEFE_NOALLOC_MAX_ATOMS and at most NEFE_NOALLOC_MAX_CELLS cells; larger
+ *   inputs return NEFE_EINVAL with a message naming the limit.
+ *   Scratch: one fixed __device__ array of about 3.6 MB in libnefe.so, held on every GPU
+ *   that loads the library until the process exits.  Every call shares it and it keeps the
+ *   previous call's contents (the occupancy counts are cleared by each call), so calls
+ *   whose GPU work may overlap (different streams, or different host threads on the same
+ *   device) race and must be serialised by the caller.  The first call on a device looks up
+ *   the array's device address (cudaGetSymbolAddress) with that device current; make that
+ *   first call before any stream capture.  Blocking: no.
+ */
+#define NEFE_NOALLOC_MAX_ATOMS 65536
+#define NEFE_NOALLOC_MAX_CELLS 65536
+NEFE_API int nefe_cell_bin_noalloc(const double* x, int n, const double box[3], double rcs,
+                                   int ncell3[3], int* cell_of, int* cell_start, int* perm,
+                                   int ncell_cap, void* stream);
+
+/*
  * nefe_neighbor_build - Verlet list with skin: for each i every j != i with minimum-image
  * d = x_j - x_i - m L, (d_x^2 + d_y^2) + d_z^2 < rcs^2 decided in FP64 (strict <), rows
  * ordered by ascending j.  (The paper relies on LAMMPS's list, Plimpton 1995; this is its

@@ -77,6 +77,7 @@ _vp = ctypes.c_void_p
 SIGNATURES = {
     "nefe_sw_params_silicon": [ctypes.POINTER(nefe_sw_params)],
     "nefe_cell_bin": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _c_int_p, _vp, _vp, _vp, ctypes.c_int, _vp],
+    "nefe_cell_bin_noalloc": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _c_int_p, _vp, _vp, _vp, ctypes.c_int, _vp],
     "nefe_neighbor_build": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, ctypes.c_int, _vp, _vp, _c_int_p, _vp],
     "nefe_sw_forces": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
                        ctypes.POINTER(nefe_sw_params), ctypes.c_int, _vp, _vp, _vp, _c_int_p, _vp],
@@ -178,6 +179,18 @@ def nefe_cell_bin(x, n, box, rcs, cell_of, cell_start, perm, ncell_cap, stream=N
     nc3 = (ctypes.c_int * 3)()
     _check(load().nefe_cell_bin(_ptr(x), int(n), _box(box), float(rcs), nc3, _ptr(cell_of),
                                 _ptr(cell_start), _ptr(perm), int(ncell_cap), _stream(stream)))
+    return tuple(nc3)
+
+
+NOALLOC_MAX_ATOMS = 65536
+NOALLOC_MAX_CELLS = 65536
+
+
+def nefe_cell_bin_noalloc(x, n, box, rcs, cell_of, cell_start, perm, ncell_cap, stream=None):
+    """Same as nefe_cell_bin without any device allocation (fixed in-library scratch)."""
+    nc3 = (ctypes.c_int * 3)()
+    _check(load().nefe_cell_bin_noalloc(_ptr(x), int(n), _box(box), float(rcs), nc3, _ptr(cell_of),
+                                        _ptr(cell_start), _ptr(perm), int(ncell_cap), _stream(stream)))
     return tuple(nc3)
 
 
