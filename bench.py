@@ -41,15 +41,21 @@ T_SW = 1000.0
 K_E = 5.0
 NSCHED = 20000
 MD_STEPS = 32       # MD steps per timed step (one graph replay)
-# Algorithmic bytes of the force kernel per atom (FP32 path, Frenkel-Ladd): own mirror 16,
-# count 4, neighbour row 4 * nbar, x 24, r0 24, v read 24, v write 24, F write 16.
-FORCE_FIXED_BYTES = 16 + 4 + 24 + 24 + 24 + 24 + 16
+# Algorithmic bytes per atom of the two force passes (FP32 path, Frenkel-Ladd):
+#   pass A (edges): own position 16 + row length 4 + neighbour row 4 nbar + partial force 16;
+#   pass B (gather): spring offset 16 + displacement 24 + noise 16 + v read 12 + v write 12
+#                    + total force write 16.
+# Whole step (the method's minimum, FP64 x and v, r0, F, list): 212 B per atom-step.
+PASS_A_FIXED = 16 + 4 + 16
+PASS_B_BYTES = 16 + 24 + 16 + 12 + 12 + 16
+STEP_BYTES = 212.0
 
 
 def workload_config(replicas):
     return {"workload": f"Frenkel-Ladd switching, {replicas} x 8000-atom Si-cd (SW), 1000 K, k=5 eV/A^2",
             "atoms_per_replica": 8 * NCELL ** 3, "replicas_per_gpu": replicas,
             "md_steps_per_step": MD_STEPS, "dt_fs": 1.0, "switch_steps": NSCHED,
+            "timed_window": "after the untimed equilibration and warm-up steps of the switching run",
             "l2": "inputs larger than L2 (no flush)"}
 
 
@@ -218,6 +224,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nefe", choices=["nefe", "reference"])
     ap.add_argument("--replicas", type=int, default=128)
+    ap.add_argument("--equil", type=int, default=3000,
+                    help="untimed MD steps before warm-up (thermalises the crystals)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -243,6 +251,7 @@ def main():
     R = args.replicas
     stream = torch.cuda.Stream()
     ctx, natoms = build_context(N, R, N.NEFE_FP32, seed0=1000 + 7919 * rank, stream=stream)
+    ctx.run(args.equil)
     lanes, tune_us = ctx.autotune()
     ctx.set_profiling(True)
     for _ in range(args.warmup):
@@ -263,8 +272,9 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = ctx.launch_count() - launches0
-    force_us, nsamp = ctx.profile()
+    a_us, b_us, nsamp = ctx.profile()
     mean_cnt, max_cnt, nbuild = ctx.list_stats(-1)
+    errors = sum(1 for r in ctx.results_all() if r["error"] != 0)
     t = torch.tensor([wall], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -272,22 +282,27 @@ def main():
     atoms = natoms * R
     value = world * atoms * MD_STEPS * args.steps / wall
 
-    # roofline of the dominant kernel (force), from its live CUDA-event durations
-    bytes_per_atom = FORCE_FIXED_BYTES + 4.0 * mean_cnt
-    achieved = bytes_per_atom * atoms / (force_us * 1e-6) / 1e9
+    # roofline of the dominant kernel (force pass A), from its live CUDA-event durations
+    bytes_a = PASS_A_FIXED + 4.0 * mean_cnt
+    achieved = bytes_a * atoms / (a_us * 1e-6) / 1e9
     peak, peak_kind = peaks()
     tr = recorded_traffic()
+    step_gbs = value / world * STEP_BYTES / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None if tr is None else tr * atoms,
-                "kernel": "k_force (SW + springs + Langevin + half kick)",
-                "algorithmic_bytes_per_atom": bytes_per_atom, "force_us_mean": force_us,
+                "kernel": "k_edges (force pass A: pair terms, triplets, leg forces)",
+                "algorithmic_bytes_per_atom": bytes_a, "kernel_us_mean": a_us,
+                "pass_b_us_mean": b_us, "pass_b_bytes_per_atom": PASS_B_BYTES,
+                "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak,
+                "step_bytes_per_atom_step": STEP_BYTES,
                 "peak_kind": f"{peak_kind} hbm_gbs", "lanes_per_atom": lanes}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": workload_config(R), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
-            "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild}}
+            "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild},
+            "systems_with_errors": errors}
     del ctx
 
     if not args.no_extras and rank == 0:
@@ -313,11 +328,13 @@ def main():
         del ctx
         # comparators on the same GPU: plain FP64 single replica, FP32 single replica, FP64 batched
         comp = {}
-        for name, reps, prec, steps in (("fp64_single_replica", 1, N.NEFE_FP64, 20),
-                                        ("fp32_single_replica", 1, N.NEFE_FP32, 20),
-                                        ("fp64_batched", R, N.NEFE_FP64, 3)):
+        for name, reps, prec, steps, eq in (("fp64_single_replica", 1, N.NEFE_FP64, 20, 1000),
+                                            ("fp32_single_replica", 1, N.NEFE_FP32, 20, 1000),
+                                            ("fp64_batched", R, N.NEFE_FP64, 3, 200)):
             s2 = torch.cuda.Stream()
             c2, na = build_context(N, reps, prec, stream=s2)
+            c2.run(eq)
+            c2.autotune()
             for _ in range(2):
                 c2.run(MD_STEPS)
             c2.sync()

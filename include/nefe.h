@@ -58,6 +58,7 @@ extern "C" {
 #define NEFE_ERR_NAN            0x4u   /* non-finite energy or pressure                  */
 #define NEFE_ERR_DEGEN          0x8u   /* dCCI singular update (see NEFE_EDEGEN)         */
 #define NEFE_ERR_BOX            0x10u  /* box below 2 (rc + skin) or cell grid too large */
+#define NEFE_ERR_CELL           0x20u  /* cell occupancy inconsistent with the atom count   */
 
 /* Precision of the force kernel.  Positions, box, energies, virial and work are FP64 in
  * both; NEFE_FP32 evaluates the pair and triplet arithmetic in FP32.                   */
@@ -135,7 +136,7 @@ NEFE_API int nefe_cell_bin_noalloc(const double* x, int n, const double box[3], 
  * plain definition.)
  *   x, n, box   as nefe_cell_bin; every box length must be >= 2 rcs.
  *   rcs         list radius rc + skin (A).
- *   cap         row capacity (1..255).
+ *   cap         row capacity (1..64).
  *   nbr         device out [n * cap] int32; entry = j | (code << 27) where
  *               code = (ox+1) + 3 (oy+1) + 9 (oz+1) is the cell offset o in {-1,0,1}^3
  *               through which j was reached: d = (x_j - q_j h) - (x_i - q_i h) + o h with
@@ -251,7 +252,7 @@ typedef struct nefe_results {
  * nefe_create - new context on CUDA device `device`, issuing work on `stream` (cudaStream_t
  * as void*, NULL = a stream the context creates).  precision: NEFE_FP32 / NEFE_FP64.
  * dt_ps: time step (the paper uses 1 fs = 0.001 ps).  skin: list skin (A).
- * nbr_cap: neighbour row capacity (16..255).
+ * nbr_cap: neighbour row capacity (16..64).
  */
 NEFE_API int nefe_create(nefe_ctx** out, int device, void* stream, int precision, double dt_ps,
                 double skin, int nbr_cap);
@@ -331,10 +332,13 @@ NEFE_API int nefe_get_list_stats(nefe_ctx* ctx, int sys, double* mean_count, int
                                  long* builds);
 
 /* Kernel timing: with profiling enabled, the captured step graph records CUDA events around
- * every force-kernel launch; nefe_get_profile returns the mean duration (us) of the force
- * launches of the most recent graph replay and how many it averaged.  Blocking. */
+ * the two force passes of every step; nefe_get_profile writes the mean time per step (us)
+ * of pass A (edges: pair terms and triplets) to us[0] and of pass B (gather, springs,
+ * Langevin, half kick) to us[1] over the steps of the most recent graph replay (each summed
+ * over the L2-sized chunks the passes run in), and the number of steps averaged.
+ * Blocking. */
 NEFE_API int nefe_set_profiling(nefe_ctx* ctx, int enable);
-NEFE_API int nefe_get_profile(nefe_ctx* ctx, double* force_us_mean, long* samples);
+NEFE_API int nefe_get_profile(nefe_ctx* ctx, double* us, long* samples);
 
 /* Number of kernel launches the context issued so far (for launch accounting). */
 NEFE_API int nefe_launch_count(nefe_ctx* ctx, long* count);

@@ -45,7 +45,11 @@ struct Scratch1 {
     void* swc = nullptr;
     int4* q = nullptr;
     void* xs = nullptr;
-    void* xsb = nullptr;
+    void* xa = nullptr;
+    void* shd = nullptr;
+    int* shj = nullptr;
+    int* shn = nullptr;
+    void* P = nullptr;
     int* cell_of = nullptr;
     int* perm = nullptr;
     int* cell_start = nullptr;
@@ -102,7 +106,7 @@ static int prepare1(Scratch1& S, int n, const double box[3], double rcs, int nce
     const size_t v4 = prec == NEFE_FP64 ? sizeof(double4) : sizeof(float4);
     NEFE_CU(S.alloc(&S.xs, v4 * (size_t)n));
     if (cells) {
-        NEFE_CU(S.alloc(&S.xsb, v4 * (size_t)n));
+        NEFE_CU(S.alloc(&S.xa, v4 * (size_t)n));
         NEFE_CU(S.alloc(&S.q, sizeof(int4) * (size_t)n));
         NEFE_CU(S.alloc(&S.cell_of, sizeof(int) * (size_t)n));
         NEFE_CU(S.alloc(&S.perm, sizeof(int) * (size_t)n));
@@ -119,7 +123,8 @@ static Bufs bufs_of(const Scratch1& S, const double* x, int n) {
     std::memset(&b, 0, sizeof(b));
     b.sys = S.sys; b.st = S.st; b.acc = S.acc; b.tile_sys = S.tile_sys;
     b.x = const_cast<double*>(x);
-    b.xs = S.xs; b.xsb = S.xsb; b.q = S.q; b.cell_of = S.cell_of; b.perm = S.perm;
+    b.xs = S.xs; b.xa = S.xa; b.q = S.q; b.cell_of = S.cell_of; b.perm = S.perm;
+    b.shd = S.shd; b.shj = S.shj; b.shn = S.shn; b.P = S.P;
     b.cell_start = S.cell_start; b.cell_count = S.cell_count; b.cell_cursor = S.cell_cursor;
     b.ntot = n; b.swc = S.swc;
     return b;
@@ -225,12 +230,18 @@ int nefe_sw_forces(const double* x, int n, const double box[3], double rcs, cons
         NEFE_CU(cudaMemcpyAsync(S.swc, &c, sizeof(c), cudaMemcpyHostToDevice, S.s));
     }
     if (n > 0) {
+        const size_t v4 = precision == NEFE_FP64 ? sizeof(double4) : sizeof(float4);
+        NEFE_CU(S.alloc(&S.shd, v4 * (size_t)n * kShell));
+        NEFE_CU(S.alloc(&S.shj, sizeof(int) * (size_t)n * kShell));
+        NEFE_CU(S.alloc(&S.shn, sizeof(int) * (size_t)n));
+        NEFE_CU(S.alloc(&S.P, v4 * (size_t)n));
         Bufs b = bufs_of(S, x, n);
         b.nbr = const_cast<int*>(nbr); b.cnt = const_cast<int*>(cnt); b.cap = cap;
         b.f_out = f; b.e_atom = e_atom;
         const int ntiles = (n + kTile - 1) / kTile;
         launch_mirror(b, precision, ntiles, S.s, nullptr);
-        launch_force(b, precision, 8, ntiles, FM_FORCES, S.s, nullptr);
+        launch_edges(b, precision, 8, ntiles, FM_FORCES, S.s, nullptr);
+        launch_gather(b, precision, ntiles, FM_FORCES, S.s, nullptr);
         NEFE_CU(cudaGetLastError());
     }
     if (energy_virial) launch_decode_ev(S.acc, energy_virial, S.s);

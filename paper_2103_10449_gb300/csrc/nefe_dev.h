@@ -12,7 +12,7 @@ constexpr double kEvA3ToGPa = 160.21766340;   // 1 eV/A^3 in GPa (1.602176634e-1
 
 constexpr int kTile = 128;        // atoms per tile; a tile never straddles two systems
 constexpr int kShell = 32;        // max neighbours inside a*sigma held per atom
-constexpr int kMaxCap = 255;      // max neighbour row capacity
+constexpr int kMaxCap = 64;       // max neighbour row capacity (one 64-bit slot mask per atom)
 constexpr int kCodeShift = 27;    // nbr entry = j | (cell-offset code << 27)
 constexpr uint32_t kIndexMask = (1u << kCodeShift) - 1u;
 
@@ -64,6 +64,10 @@ struct DevSys {
     double amp;                 // Langevin noise amplitude sqrt(2 m kB T / (tdamp dt)) (eV/A)
     double gam;                 // Langevin friction m / tdamp (eV ps / A^2)
     double ckick;               // dt / (2 m) (A^2 / (eV ps))
+    // FP32 copies and flags read by the FP32 kernels (no FP64 instruction per atom)
+    float amp_f, gam_f, ckick_f, mass_f, kE_f, kint_f, dt_f, inv_n_f;
+    int thermo;                 // tdamp > 0
+    int springs;                // an Einstein spring acts (FL reference or U_int = Einstein)
     int trace_every;
     long long trace_cap, trace_off;
     int prm;                    // index into the parameter tables
@@ -89,6 +93,11 @@ struct DevState {
     int pad;
     long long trace_n;
     long long nbuild;           // list builds so far
+    // FP32 copies of this step's constants (written with their FP64 sources)
+    float h_f[3], hb_f[3], rho_f[3], phi_f[3], sm1_f[3];
+    float scale_int_f, scale_E_f, thr2_f;
+    int scaled;                 // s != 1 on some axis (barostat moved the box this step)
+    int hmoved;                 // h != hb on some axis (box differs from the last build)
 };
 
 struct DevPair {

@@ -17,7 +17,11 @@ using namespace nefe;
 namespace {
 
 constexpr int kGraphSteps = 32;
-constexpr int kLaunchesPerStep = 8;   // group, kick-drift, 5 rebuild kernels, force
+// The two force passes run chunk by chunk (whole systems, at most this many atoms) so that
+// the shells pass A writes are still in L2 when pass B reads them.
+constexpr int kChunkAtoms = 1 << 18;
+// launches per step: group, kick-drift, 6 rebuild kernels, then 2 force passes per chunk
+int launches_per_step(const nefe_ctx* c);
 
 struct HostSys {
     int n = 0;
@@ -62,8 +66,11 @@ struct nefe_ctx {
     long long* d_acc = nullptr;
     long long* d_acc_tmp = nullptr;
     int* d_tile_sys = nullptr;
-    double *d_x = nullptr, *d_v = nullptr, *d_r0 = nullptr, *d_ftmp = nullptr;
-    void *d_F = nullptr, *d_xs = nullptr, *d_xsb = nullptr;
+    double *d_x = nullptr, *d_r0 = nullptr, *d_ftmp = nullptr, *d_vtmp = nullptr;
+    void *d_v = nullptr, *d_dhi = nullptr, *d_dlo = nullptr;
+    void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
+    void *d_shd = nullptr, *d_P = nullptr;
+    int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr;
     int4* d_q = nullptr;
     int *d_cell_of = nullptr, *d_perm = nullptr, *d_cell_start = nullptr, *d_cell_count = nullptr,
         *d_cell_cursor = nullptr, *d_nbr = nullptr, *d_cnt = nullptr;
@@ -78,11 +85,14 @@ struct nefe_ctx {
     cudaGraphExec_t gexec = nullptr;
     long launches = 0;
     bool profiling = false;
-    std::vector<cudaEvent_t> ev0, ev1;   // around each force launch of the captured graph
+    std::vector<cudaEvent_t> ev0, ev1, ev2;   // around the force passes of the captured graph
+    std::vector<int> chunk_tile0, chunk_ntile;
     Bufs b{};
 };
 
 namespace {
+
+int launches_per_step(const nefe_ctx* c) { return 8 + 2 * (int)c->chunk_tile0.size(); }
 
 int set_device(nefe_ctx* c) {
     NEFE_CU(cudaSetDevice(c->device));
@@ -112,14 +122,28 @@ int not_ready(nefe_ctx* c, const char* what) {
 
 double rc_of(const HostSys& h) { return h.prm.a * h.prm.sigma; }
 
+// Both force passes, chunk by chunk; with slot >= 0 (profiling capture) events bracket
+// every chunk's pass A and pass B.
+void enqueue_forces(nefe_ctx* c, int mode, int slot = -1) {
+    const int nch = (int)c->chunk_tile0.size();
+    for (int k = 0; k < nch; ++k) {
+        Bufs b = c->b;
+        b.tile_base = c->chunk_tile0[k];
+        const int e = slot >= 0 ? slot * nch + k : -1;
+        const bool prof = e >= 0 && e < (int)c->ev0.size();
+        if (prof) cudaEventRecordWithFlags(c->ev0[e], c->stream, cudaEventRecordExternal);
+        launch_edges(b, c->prec, c->lanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
+        if (prof) cudaEventRecordWithFlags(c->ev1[e], c->stream, cudaEventRecordExternal);
+        launch_gather(b, c->prec, c->chunk_ntile[k], mode, c->stream, &c->launches);
+        if (prof) cudaEventRecordWithFlags(c->ev2[e], c->stream, cudaEventRecordExternal);
+    }
+}
+
 void enqueue_step(nefe_ctx* c, int slot = -1) {
     launch_group(c->b, c->d_groups, c->ngroups, 1, c->stream, &c->launches);
     launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches);
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
-    const bool prof = slot >= 0 && slot < (int)c->ev0.size();
-    if (prof) cudaEventRecordWithFlags(c->ev0[slot], c->stream, cudaEventRecordExternal);
-    launch_force(c->b, c->prec, c->lanes, c->ntiles, FM_STEP, c->stream, &c->launches);
-    if (prof) cudaEventRecordWithFlags(c->ev1[slot], c->stream, cudaEventRecordExternal);
+    enqueue_forces(c, FM_STEP, slot);
 }
 
 void fill_results(const DevSys& S, const DevState& st, nefe_results* out) {
@@ -155,7 +179,7 @@ int resetup(nefe_ctx* c) {
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * (size_t)c->nsys * ACC_N * kSlots, c->stream));
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 1, c->stream, &c->launches);
     launch_kick_drift(c->b, c->prec, c->ntiles, 0, c->stream, &c->launches);
-    launch_force(c->b, c->prec, c->lanes, c->ntiles, FM_SETUP, c->stream, &c->launches);
+    enqueue_forces(c, FM_SETUP);
     NEFE_CU(cudaGetLastError());
     return NEFE_OK;
 }
@@ -220,6 +244,12 @@ int setup(nefe_ctx* c) {
         d.amp = h.tdamp > 0.0 ? std::sqrt(2.0 * d.mass_e * kB * h.T / (h.tdamp * c->dt)) : 0.0;
         d.gam = h.tdamp > 0.0 ? d.mass_e / h.tdamp : 0.0;
         d.ckick = 0.5 * c->dt / d.mass_e;
+        d.amp_f = (float)d.amp; d.gam_f = (float)d.gam; d.ckick_f = (float)d.ckick;
+        d.mass_f = (float)d.mass_e; d.kE_f = (float)d.k_E; d.kint_f = (float)d.k_int;
+        d.dt_f = (float)c->dt;
+        d.inv_n_f = (float)(1.0 / h.n);
+        d.thermo = h.tdamp > 0.0 ? 1 : 0;
+        d.springs = (d.k_E > 0.0 || h.pot == NEFE_POT_EINSTEIN) ? 1 : 0;
         d.trace_every = h.trace_every;
         d.trace_cap = h.trace_cap;
         d.trace_off = tr;
@@ -234,6 +264,22 @@ int setup(nefe_ctx* c) {
         tr += h.trace_every > 0 ? h.trace_cap : 0;
     }
     if (ntot >= (1LL << kCodeShift)) return fail(NEFE_EINVAL, "more than 2^27 atoms in one context");
+    c->chunk_tile0.clear();
+    c->chunk_ntile.clear();
+    {
+        int t0 = 0, atoms = 0;
+        for (int s = 0; s < nsys; ++s) {
+            if (atoms > 0 && atoms + hs[s].n > kChunkAtoms) {
+                c->chunk_tile0.push_back(t0);
+                c->chunk_ntile.push_back(hs[s].tile0 - t0);
+                t0 = hs[s].tile0;
+                atoms = 0;
+            }
+            atoms += hs[s].n;
+        }
+        c->chunk_tile0.push_back(t0);
+        c->chunk_ntile.push_back((int)tile_sys.size() - t0);
+    }
     c->ntot = (int)ntot;
     c->ntiles = (int)tile_sys.size();
     c->nsys = nsys;
@@ -262,18 +308,30 @@ int setup(nefe_ctx* c) {
 
     const size_t N = (size_t)ntot;
     const size_t v4 = c->prec == NEFE_FP64 ? sizeof(double4) : sizeof(float4);
+    const size_t el = c->prec == NEFE_FP64 ? sizeof(double) : sizeof(float);
     if ((rc = dalloc(c, &c->d_sys, sizeof(DevSys) * nsys))) return rc;
     if ((rc = dalloc(c, &c->d_st, sizeof(DevState) * nsys))) return rc;
     if ((rc = dalloc(c, &c->d_acc, sizeof(long long) * nsys * ACC_N * kSlots))) return rc;
     if ((rc = dalloc(c, &c->d_acc_tmp, sizeof(long long) * nsys * ACC_N * kSlots))) return rc;
     if ((rc = dalloc(c, &c->d_tile_sys, sizeof(int) * tile_sys.size()))) return rc;
     if ((rc = dalloc(c, &c->d_x, sizeof(double) * 3 * N))) return rc;
-    if ((rc = dalloc(c, &c->d_v, sizeof(double) * 3 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_v, el * 3 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_dhi, el * 3 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_dlo, el * 3 * N))) return rc;
     if ((rc = dalloc(c, &c->d_r0, sizeof(double) * 3 * N))) return rc;
     if ((rc = dalloc(c, &c->d_ftmp, sizeof(double) * 3 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_vtmp, sizeof(double) * 3 * N))) return rc;
     if ((rc = dalloc(c, &c->d_F, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_xs, v4 * N))) return rc;
-    if ((rc = dalloc(c, &c->d_xsb, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_xa, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_sd0, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_xi, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_shd, v4 * N * (size_t)kShell))) return rc;
+    if ((rc = dalloc(c, &c->d_shj, sizeof(int) * N * (size_t)kShell))) return rc;
+    if ((rc = dalloc(c, &c->d_shn, sizeof(int) * N))) return rc;
+    if ((rc = dalloc(c, &c->d_P, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_rtiles, sizeof(int) * tile_sys.size()))) return rc;
+    if ((rc = dalloc(c, &c->d_rcount, sizeof(int)))) return rc;
     if ((rc = dalloc(c, &c->d_q, sizeof(int4) * N))) return rc;
     if ((rc = dalloc(c, &c->d_cell_of, sizeof(int) * N))) return rc;
     if ((rc = dalloc(c, &c->d_perm, sizeof(int) * N))) return rc;
@@ -309,8 +367,11 @@ int setup(nefe_ctx* c) {
             }
     }
     NEFE_CU(cudaMemcpy(c->d_x, hx.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
-    NEFE_CU(cudaMemcpy(c->d_v, hv.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
+    NEFE_CU(cudaMemcpy(c->d_vtmp, hv.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
     NEFE_CU(cudaMemcpy(c->d_r0, hr.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
+    NEFE_CU(cudaMemset(c->d_dhi, 0, el * 3 * N));
+    NEFE_CU(cudaMemset(c->d_dlo, 0, el * 3 * N));
+    NEFE_CU(cudaMemset(c->d_xi, 0, v4 * N));
     NEFE_CU(cudaMemcpy(c->d_sys, hs.data(), sizeof(DevSys) * nsys, cudaMemcpyHostToDevice));
     NEFE_CU(cudaMemcpy(c->d_st, hst.data(), sizeof(DevState) * nsys, cudaMemcpyHostToDevice));
     NEFE_CU(cudaMemcpy(c->d_tile_sys, tile_sys.data(), sizeof(int) * tile_sys.size(), cudaMemcpyHostToDevice));
@@ -324,12 +385,16 @@ int setup(nefe_ctx* c) {
     Bufs& b = c->b;
     std::memset(&b, 0, sizeof(b));
     b.sys = c->d_sys; b.st = c->d_st; b.acc = c->d_acc; b.tile_sys = c->d_tile_sys;
-    b.x = c->d_x; b.v = c->d_v; b.r0 = c->d_r0; b.F = c->d_F; b.xs = c->d_xs; b.xsb = c->d_xsb;
+    b.x = c->d_x; b.v = c->d_v; b.dhi = c->d_dhi; b.dlo = c->d_dlo; b.r0 = c->d_r0; b.F = c->d_F;
+    b.xs = c->d_xs; b.xa = c->d_xa; b.sd0 = c->d_sd0; b.xi = c->d_xi;
+    b.shd = c->d_shd; b.shj = c->d_shj; b.shn = c->d_shn; b.P = c->d_P;
+    b.rtiles = c->d_rtiles; b.rcount = c->d_rcount;
     b.q = c->d_q; b.cell_of = c->d_cell_of; b.perm = c->d_perm; b.cell_start = c->d_cell_start;
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;
     b.trace = c->d_trace;
 
+    launch_inject(b, c->prec, c->ntiles, nullptr, c->d_vtmp, c->stream);
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * nsys * ACC_N * kSlots, c->stream));
     launch_group(b, c->d_groups, c->ngroups, 0, c->stream, &c->launches);
     c->ready = true;
@@ -349,7 +414,7 @@ int nefe_create(nefe_ctx** out, int device, void* stream, int precision, double 
     *out = nullptr;
     if (precision != NEFE_FP32 && precision != NEFE_FP64) return fail(NEFE_EINVAL, "bad precision");
     if (!(dt_ps > 0.0) || !(skin > 0.0)) return fail(NEFE_EINVAL, "dt and skin must be positive");
-    if (nbr_cap < 16 || nbr_cap > kMaxCap) return fail(NEFE_EINVAL, "nbr_cap must be in 16..255");
+    if (nbr_cap < 16 || nbr_cap > kMaxCap) return fail(NEFE_EINVAL, "nbr_cap must be in 16..64");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -384,6 +449,7 @@ int nefe_destroy(nefe_ctx* c) {
     drop_graph(c);
     for (auto e : c->ev0) cudaEventDestroy(e);
     for (auto e : c->ev1) cudaEventDestroy(e);
+    for (auto e : c->ev2) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -531,7 +597,7 @@ int nefe_run(nefe_ctx* c, long nsteps) {
     }
     for (long f = 0; f < full; ++f) {
         NEFE_CU(cudaGraphLaunch(c->gexec, c->stream));
-        c->launches += (long)kGraphSteps * kLaunchesPerStep;
+        c->launches += (long)kGraphSteps * launches_per_step(c);
     }
     for (long r = 0; r < rem; ++r) enqueue_step(c);
     NEFE_CU(cudaGetLastError());
@@ -586,12 +652,13 @@ int nefe_get_state(nefe_ctx* c, int s, double* x, double* v, double* box) {
     const int n = c->sys[s].n;
     DevSys S;
     NEFE_CU(cudaMemcpyAsync(&S, c->d_sys + s, sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+    launch_materialize(c->b, c->prec, c->ntiles, c->d_ftmp, c->d_vtmp, c->stream);
     NEFE_CU(cudaStreamSynchronize(c->stream));
     std::vector<double> tmp(3 * (size_t)n);
     const size_t N = c->ntot;
     for (int which = 0; which < 2; ++which) {
         double* dst = which == 0 ? x : v;
-        const double* src = which == 0 ? c->d_x : c->d_v;
+        const double* src = which == 0 ? c->d_ftmp : c->d_vtmp;
         if (!dst) continue;
         for (int k = 0; k < 3; ++k)
             NEFE_CU(cudaMemcpyAsync(tmp.data() + (size_t)k * n, src + k * N + S.off, sizeof(double) * n,
@@ -618,11 +685,13 @@ int nefe_set_state(nefe_ctx* c, int s, const double* x, const double* v) {
     const size_t N = c->ntot;
     DevSys S;
     NEFE_CU(cudaMemcpyAsync(&S, c->d_sys + s, sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+    // current state of every system, then this system's slice replaced
+    launch_materialize(c->b, c->prec, c->ntiles, c->d_ftmp, c->d_vtmp, c->stream);
     NEFE_CU(cudaStreamSynchronize(c->stream));
     std::vector<double> tmp(3 * (size_t)n);
     for (int which = 0; which < 2; ++which) {
         const double* src = which == 0 ? x : v;
-        double* dst = which == 0 ? c->d_x : c->d_v;
+        double* dst = which == 0 ? c->d_ftmp : c->d_vtmp;
         if (!src) continue;
         for (int i = 0; i < n; ++i)
             for (int k = 0; k < 3; ++k) tmp[(size_t)k * n + i] = src[3 * i + k];
@@ -631,6 +700,7 @@ int nefe_set_state(nefe_ctx* c, int s, const double* x, const double* v) {
                                     cudaMemcpyHostToDevice, c->stream));
         NEFE_CU(cudaStreamSynchronize(c->stream));
     }
+    launch_inject(c->b, c->prec, c->ntiles, x ? c->d_ftmp : nullptr, v ? c->d_vtmp : nullptr, c->stream);
     return resetup(c);
 }
 
@@ -670,14 +740,19 @@ struct Blob {
 static std::vector<Blob> blobs(nefe_ctx* c) {
     const size_t N = c->ntot;
     const size_t v4 = c->prec == NEFE_FP64 ? sizeof(double4) : sizeof(float4);
+    const size_t el = c->prec == NEFE_FP64 ? sizeof(double) : sizeof(float);
     return {{c->d_st, sizeof(DevState) * c->nsys},
             {c->d_acc, sizeof(long long) * c->nsys * ACC_N * kSlots},
             {c->d_pairs, sizeof(DevPair) * std::max<size_t>(1, c->pairs.size())},
             {c->d_x, sizeof(double) * 3 * N},
-            {c->d_v, sizeof(double) * 3 * N},
+            {c->d_v, el * 3 * N},
+            {c->d_dhi, el * 3 * N},
+            {c->d_dlo, el * 3 * N},
             {c->d_F, v4 * N},
             {c->d_xs, v4 * N},
-            {c->d_xsb, v4 * N},
+            {c->d_xa, v4 * N},
+            {c->d_sd0, v4 * N},
+            {c->d_xi, v4 * N},
             {c->d_q, sizeof(int4) * N},
             {c->d_cell_of, sizeof(int) * N},
             {c->d_perm, sizeof(int) * N},
@@ -753,10 +828,10 @@ int nefe_autotune(nefe_ctx* c) {
     int best_l = c->lanes;
     for (int l : cand) {
         if (c->prec == NEFE_FP64 && l == 4) continue;
-        for (int w = 0; w < 2; ++w) launch_force(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches);
+        for (int w = 0; w < 2; ++w) launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches);
         cudaEventRecord(e0, c->stream);
         const int reps = 5;
-        for (int r = 0; r < reps; ++r) launch_force(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches);
+        for (int r = 0; r < reps; ++r) launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches);
         cudaEventRecord(e1, c->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
@@ -798,9 +873,11 @@ int nefe_set_state_all(nefe_ctx* c, const double* x, const double* v) {
     for (int which = 0; which < 2; ++which) {
         const double* src = which == 0 ? x : v;
         if (!src) continue;
-        NEFE_CU(cudaMemcpyAsync(c->d_ftmp, src, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->stream));
-        launch_aos_soa(c->d_ftmp, which == 0 ? c->d_x : c->d_v, (int)N, 1, c->stream);
+        // host (N,3) -> device staging -> SoA -> state
+        NEFE_CU(cudaMemcpyAsync(c->d_shd, src, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->stream));
+        launch_aos_soa(static_cast<const double*>(c->d_shd), which == 0 ? c->d_ftmp : c->d_vtmp, (int)N, 1, c->stream);
     }
+    launch_inject(c->b, c->prec, c->ntiles, x ? c->d_ftmp : nullptr, v ? c->d_vtmp : nullptr, c->stream);
     return resetup(c);
 }
 
@@ -810,11 +887,13 @@ int nefe_get_state_all(nefe_ctx* c, double* x, double* v) {
     if (rc) return rc;
     if ((rc = set_device(c))) return rc;
     const size_t N = c->ntot;
+    launch_materialize(c->b, c->prec, c->ntiles, c->d_ftmp, c->d_vtmp, c->stream);
     for (int which = 0; which < 2; ++which) {
         double* dst = which == 0 ? x : v;
         if (!dst) continue;
-        launch_aos_soa(which == 0 ? c->d_x : c->d_v, c->d_ftmp, (int)N, 0, c->stream);
-        NEFE_CU(cudaMemcpyAsync(dst, c->d_ftmp, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+        double* stage = static_cast<double*>(c->d_shd);
+        launch_aos_soa(which == 0 ? c->d_ftmp : c->d_vtmp, stage, (int)N, 0, c->stream);
+        NEFE_CU(cudaMemcpyAsync(dst, stage, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
     }
     NEFE_CU(cudaStreamSynchronize(c->stream));
     return NEFE_OK;
@@ -881,34 +960,51 @@ int nefe_set_profiling(nefe_ctx* c, int enable) {
     drop_graph(c);
     c->profiling = enable != 0;
     if (c->profiling && c->ev0.empty()) {
-        c->ev0.resize(kGraphSteps);
-        c->ev1.resize(kGraphSteps);
-        for (int k = 0; k < kGraphSteps; ++k) {
+        const int ne = kGraphSteps * std::max<int>(1, (int)c->chunk_tile0.size());
+        c->ev0.resize(ne);
+        c->ev1.resize(ne);
+        c->ev2.resize(ne);
+        for (int k = 0; k < ne; ++k) {
             NEFE_CU(cudaEventCreate(&c->ev0[k]));
             NEFE_CU(cudaEventCreate(&c->ev1[k]));
+            NEFE_CU(cudaEventCreate(&c->ev2[k]));
         }
     }
     return NEFE_OK;
 }
 
-int nefe_get_profile(nefe_ctx* c, double* force_us_mean, long* samples) {
+int nefe_get_profile(nefe_ctx* c, double* us, long* samples) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     if (!c->profiling || c->ev0.empty()) return fail(NEFE_ESTATE, "profiling is not enabled");
     int rc = set_device(c);
     if (rc) return rc;
     NEFE_CU(cudaStreamSynchronize(c->stream));
-    double tot = 0.0;
+    // per step: the sum over chunks of each pass
+    const int nch = std::max<int>(1, (int)c->chunk_tile0.size());
+    double ta = 0.0, tb = 0.0;
     long n = 0;
     for (int k = 0; k < kGraphSteps; ++k) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->ev0[k], c->ev1[k]) == cudaSuccess) {
-            tot += ms;
-            ++n;
-        } else {
-            cudaGetLastError();
+        bool ok = true;
+        double sa = 0.0, sb = 0.0;
+        for (int q = 0; q < nch && ok; ++q) {
+            const int e = k * nch + q;
+            if (e >= (int)c->ev0.size()) { ok = false; break; }
+            float ma = 0.f, mb = 0.f;
+            if (cudaEventElapsedTime(&ma, c->ev0[e], c->ev1[e]) != cudaSuccess ||
+                cudaEventElapsedTime(&mb, c->ev1[e], c->ev2[e]) != cudaSuccess) {
+                cudaGetLastError();
+                ok = false;
+                break;
+            }
+            sa += ma;
+            sb += mb;
         }
+        if (ok) { ta += sa; tb += sb; ++n; }
     }
-    if (force_us_mean) *force_us_mean = n > 0 ? 1000.0 * tot / n : 0.0;
+    if (us) {
+        us[0] = n > 0 ? 1000.0 * ta / n : 0.0;
+        us[1] = n > 0 ? 1000.0 * tb / n : 0.0;
+    }
     if (samples) *samples = n;
     return NEFE_OK;
 }

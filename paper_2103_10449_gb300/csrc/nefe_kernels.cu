@@ -5,11 +5,23 @@
 //                 P, V, dH/dl, records, kicks the barostat, advances lambda and W (Eq. Wdyn,
 //                 left point), applies the dCCI update (Eqs. Ps_coex_discreted /
 //                 l_coex_discreted), sets this step's drift factors and zeroes the sums.
-//   k_kick_drift  v += dt/2 F/m; x = s x + dt phi v (affine box drift); FP32/FP64 mirror
-//                 xs = x - q h; displacement test -> rebuild flag; sum of thermostat noise.
-//   rebuild       (flagged systems) cell count -> scan -> fill -> per-cell sort -> list.
-//   k_force       SW pair + triplet gather (FP32 or FP64), Einstein springs (FP64), lambda
-//                 mixing, Langevin force with its mean removed, second half kick, sums.
+//   k_kick_drift  v += dt/2 F/m; displacement since the last list build += dt phi v (+ the
+//                 affine box drift), kept as a compensated pair in the FP32 path; mirror
+//                 xs = x - q h; displacement test -> rebuild flag; thermostat noise + its sum.
+//   rebuild       (flagged systems) fold the displacement into the FP64 anchor, cell count ->
+//                 scan -> fill -> per-cell sort -> Verlet list.
+//   k_edges       force pass A: in-cutoff shell of each atom (stored compactly), pair terms,
+//                 the triplets centred on the atom (force on it, energy, virial).
+//   k_gather      force pass B: the atom's pass-A force plus, from the stored shells, the
+//                 force of every triplet centred on a neighbour in which the atom is a leg
+//                 (a gather: no atomics, bitwise reproducible); Einstein springs, lambda
+//                 mixing, Langevin force with its per-system mean removed, second half kick.
+//
+// Positions: the FP64 anchor x (positions at the last list build) plus the displacement
+// since then (FP64, or an FP32 value + FP32 compensation term, ~2^-48 relative).  The anchor
+// absorbs the displacement at every list build, so the per-step path of the FP32 kernels
+// issues no FP64 instruction (GB300 runs FP64 at 1/64 of the FP32 rate): per-system
+// constants are read from FP32 copies written once per step by k_group.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +37,23 @@ template <> struct V4<double> { using t = double4; };
 
 __device__ __forceinline__ float4 mk4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 __device__ __forceinline__ double4 mk4(double a, double b, double c, double d) { return make_double4(a, b, c, d); }
+
+// Precision-explicit math (no silent promotion of FP32 arguments to the FP64 routines).
+// The FP32 path uses the hardware approximations (MUFU: ex2, rcp, rsqrt; a few ulp, far
+// inside the 1e-5 relative force tolerance); the FP64 path the correctly rounded routines.
+__device__ __forceinline__ float xexp(float v) { return __expf(v); }
+__device__ __forceinline__ double xexp(double v) { return ::exp(v); }
+__device__ __forceinline__ float xrcp(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double xrcp(double v) { return 1.0 / v; }
+__device__ __forceinline__ float xrsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double xrsqrt(double v) { return ::rsqrt(v); }
+__device__ __forceinline__ float xpow(float a, float b) { return __powf(a, b); }
+__device__ __forceinline__ double xpow(double a, double b) { return ::pow(a, b); }
+
+// FP32 copy or FP64 source of a constant, by kernel precision.
+template <typename T> __device__ __forceinline__ T pick(double d, float f) {
+    if constexpr (sizeof(T) == 4) return f; else return d;
+}
 
 // ------------------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): round (hi0,lo0) = M0 X0,
@@ -55,10 +84,10 @@ template <> struct Noise<double> {
         const double u2 = ((double)(c[2] >> 11) + 0.5) * 0x1p-53;
         const double u3 = ((double)(c[3] >> 11) + 0.5) * 0x1p-53;
         const double two_pi = 6.283185307179586476925286766559;
-        const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+        const double r0 = ::sqrt(-2.0 * ::log(u0)), r1 = ::sqrt(-2.0 * ::log(u2));
         double s0, c0, s1, c1;
-        sincos(two_pi * u1, &s0, &c0);
-        sincos(two_pi * u3, &s1, &c1);
+        ::sincos(two_pi * u1, &s0, &c0);
+        ::sincos(two_pi * u3, &s1, &c1);
         out[0] = r0 * c0; out[1] = r0 * s0; out[2] = r1 * c1;
     }
 };
@@ -66,10 +95,10 @@ template <> struct Noise<float> {
     __device__ static void xi3(uint64_t seed, uint64_t sys, uint64_t step, uint64_t id, float out[3]) {
         uint64_t c[4] = {step, id, sys, 0ULL};
         philox4x64_10(c, seed, 0ULL);
-        const float u0 = ((float)(c[0] >> 40) + 0.5f) * 0x1p-24f;
-        const float u1 = ((float)(c[1] >> 40) + 0.5f) * 0x1p-24f;
-        const float u2 = ((float)(c[2] >> 40) + 0.5f) * 0x1p-24f;
-        const float u3 = ((float)(c[3] >> 40) + 0.5f) * 0x1p-24f;
+        const float u0 = ((float)(uint32_t)(c[0] >> 40) + 0.5f) * 0x1p-24f;
+        const float u1 = ((float)(uint32_t)(c[1] >> 40) + 0.5f) * 0x1p-24f;
+        const float u2 = ((float)(uint32_t)(c[2] >> 40) + 0.5f) * 0x1p-24f;
+        const float u3 = ((float)(uint32_t)(c[3] >> 40) + 0.5f) * 0x1p-24f;
         const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
         float s0, c0, s1, c1;
         sincospif(2.0f * u1, &s0, &c0);
@@ -79,35 +108,59 @@ template <> struct Noise<float> {
 };
 
 // ------------------------------------------------------------------------------------
-// Deterministic per-system sums: warp shuffle -> shared -> one int64 fixed-point atomic per
-// value into slot (blockIdx % kSlots).  Every thread of the block must call it.
+// Deterministic per-system sums: warp shuffle in kernel precision -> FP64 across warps ->
+// one int64 fixed-point atomic per value into slot (blockIdx % kSlots).  Every thread of
+// the block must call it.
 // ------------------------------------------------------------------------------------
 template <typename T, int K>
 __device__ __forceinline__ void block_sum_to_acc(T (&v)[K], long long* acc_sys, int first,
                                                  unsigned* err) {
-    __shared__ double red[kTile / 32][K];
+    __shared__ T red[kTile / 32][K];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         T x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[w][k] = (double)x;
+        if (lane == 0) red[w][k] = x;
     }
     __syncthreads();
     if (threadIdx.x < K) {
-        double s = 0.0;
+        T s = 0;
 #pragma unroll
         for (int i = 0; i < kTile / 32; ++i) s += red[i][threadIdx.x];
-        if (!isfinite(s)) {
+        long long q;
+        bool bad;
+        if constexpr (sizeof(T) == 4) {
+            // round(s 2^16) in int32 (|s| < 32768 per block), moved to the 2^-32 scale
+            const float t = s * 65536.0f;
+            bad = !(fabsf(t) < 2147483520.0f);
+            q = bad ? 0LL : (long long)__float2int_rn(t) * 65536LL;
+        } else {
+            bad = !isfinite(s);
+            q = bad ? 0LL : __double2ll_rn(s * kFix);
+        }
+        if (bad) {
             atomicOr(err, NEFE_ERR_NAN);
-        } else if (s != 0.0) {
-            const long long q = __double2ll_rn(s * kFix);
+        } else if (q != 0) {
             atomicAdd(reinterpret_cast<unsigned long long*>(
                           &acc_sys[(size_t)(first + threadIdx.x) * kSlots + (blockIdx.x % kSlots)]),
                       (unsigned long long)q);
         }
     }
+}
+
+// Per-block table of the 27 cell-offset vectors o h (o in {-1,0,1}^3), indexed by the list
+// entry's code.  Every thread of the block must call it.
+template <typename T>
+__device__ __forceinline__ void offset_table(typename V4<T>::t* tab, T hx, T hy, T hz) {
+    if (threadIdx.x < 27) {
+        const int c = threadIdx.x;
+        const int ox = c % 3 - 1, oy = (c / 3) % 3 - 1, oz = c / 9 - 1;
+        tab[c] = mk4(ox == 0 ? (T)0 : (ox < 0 ? -hx : hx), oy == 0 ? (T)0 : (oy < 0 ? -hy : hy),
+                     oz == 0 ? (T)0 : (oz < 0 ? -hz : hz), (T)0);
+    }
+    __syncthreads();
 }
 
 // Cell grid for a box: per axis floor(L/rcs), reduced while L/n < rcs (1 + 1e-9); then the
@@ -128,6 +181,18 @@ __device__ __forceinline__ bool grid_for(const double box[3], double rcs, int ca
     return ok;
 }
 
+// FP32 copies of the box-dependent constants (called wherever h or hb change).
+__device__ __forceinline__ void refresh_box_f(DevState& st) {
+    bool hm = false;
+    for (int k = 0; k < 3; ++k) {
+        st.h_f[k] = (float)st.h[k];
+        st.hb_f[k] = (float)st.hb[k];
+        st.rho_f[k] = (float)(st.h[k] / st.hb[k]);
+        hm = hm || (st.h[k] != st.hb[k]);
+    }
+    st.hmoved = hm ? 1 : 0;
+}
+
 struct TileAtom {
     int sys, first, count;
 };
@@ -141,31 +206,42 @@ __device__ __forceinline__ TileAtom tile_of(const Bufs& b, int tile) {
 }
 
 // ------------------------------------------------------------------------------------
-// Rebuild: R1 cell of each atom, unwrapped cell index q, fresh mirror, occupancy count.
-// The cell formula is c = (int)(w n) with w = x/L - floor(x/L) evaluated in FP64.
+// Rebuild R1: fold the displacement into the FP64 anchor; cell of each atom, unwrapped cell
+// index q, fresh mirror, spring offset, occupancy count.  The cell formula is
+// c = (int)(w n) with w = x/L - floor(x/L) evaluated in FP64.
 // ------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kTile) k_cells_count(Bufs b, int force_all) {
+__device__ void cells_count_tile(const Bufs& b, int tile) {
     using T4 = typename V4<T>::t;
-    const TileAtom ta = tile_of(b, blockIdx.x);
+    const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
-    if (!force_all && !st.rebuild) return;
     int n3[3];
     const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, n3);
     double h[3];
     for (int k = 0; k < 3; ++k) h[k] = __ddiv_rn(st.box[k], (double)n3[k]);
-    if (blockIdx.x == S.tile0 && threadIdx.x == 0) {
+    if (tile == S.tile0 && threadIdx.x == 0) {
         for (int k = 0; k < 3; ++k) { st.ncell[k] = n3[k]; st.h[k] = h[k]; st.hb[k] = h[k]; }
+        refresh_box_f(st);
         st.nbuild += 1;
         if (!ok) atomicOr(&st.err, NEFE_ERR_BOX);
     }
     if ((int)threadIdx.x >= ta.count) return;
     const int i = ta.first + threadIdx.x;
+    const size_t N = b.ntot;
     int c3[3], qv[3];
-    double xs[3];
+    double xm[3], sd[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < 3; ++k) {
-        const double xk = b.x[(size_t)k * b.ntot + i];
+        double xk = b.x[k * N + i];
+        if (b.dhi) {   // fold the displacement into the FP64 anchor
+            T* dh = reinterpret_cast<T*>(b.dhi);
+            T* dl = reinterpret_cast<T*>(b.dlo);
+            const double d = (double)dh[k * N + i] + (b.dlo ? (double)dl[k * N + i] : 0.0);
+            xk = xk + d;
+            b.x[k * N + i] = xk;
+            dh[k * N + i] = (T)0;
+            if (b.dlo) dl[k * N + i] = (T)0;
+        }
         const double s = __ddiv_rn(xk, st.box[k]);
         const double fl = floor(s);
         const double w = __dsub_rn(s, fl);
@@ -174,15 +250,55 @@ __global__ void __launch_bounds__(kTile) k_cells_count(Bufs b, int force_all) {
         if (c < 0) c = 0;
         c3[k] = c;
         qv[k] = (int)fl * n3[k] + c;
-        xs[k] = xk - (double)qv[k] * h[k];
+        xm[k] = xk - (double)qv[k] * h[k];
+        if (b.r0) sd[k] = xk - b.r0[k * N + i];
     }
     const int cell = c3[0] + n3[0] * (c3[1] + n3[1] * c3[2]);
     b.cell_of[i] = cell;
     b.q[i] = make_int4(qv[0], qv[1], qv[2], 0);
-    const T4 m = mk4((T)xs[0], (T)xs[1], (T)xs[2], (T)0);
+    const T4 m = mk4((T)xm[0], (T)xm[1], (T)xm[2], (T)0);
     reinterpret_cast<T4*>(b.xs)[i] = m;
-    reinterpret_cast<T4*>(b.xsb)[i] = m;
+    if (b.xa) reinterpret_cast<T4*>(b.xa)[i] = m;
+    if (b.sd0) reinterpret_cast<T4*>(b.sd0)[i] = mk4((T)sd[0], (T)sd[1], (T)sd[2], (T)0);
     atomicAdd(&b.cell_count[S.cell0 + cell], 1);
+}
+
+// The rebuild kernels walk a worklist of the tiles of flagged systems (written by
+// k_rebuild_list) with a bounded grid, or every tile (stateless calls: no worklist).
+#define NEFE_FOR_TILES(b, body_call)                                           \
+    do {                                                                      \
+        if ((b).rtiles) {                                                     \
+            const int n_ = *(b).rcount;                                       \
+            for (int w_ = blockIdx.x; w_ < n_; w_ += gridDim.x) {             \
+                const int tile = (b).rtiles[w_];                              \
+                body_call;                                                    \
+            }                                                                 \
+        } else {                                                              \
+            const int tile = blockIdx.x;                                      \
+            body_call;                                                        \
+        }                                                                     \
+    } while (0)
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_cells_count(Bufs b) {
+    NEFE_FOR_TILES(b, cells_count_tile<T>(b, tile));
+}
+
+// Worklist of the tiles of every system whose rebuild flag is set (all with force_all).
+// Tile order in the list does not matter: every tile is processed independently.
+__global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+        if (force_all || b.st[s].rebuild) {
+            const DevSys& S = b.sys[s];
+            const int base = atomicAdd(&cnt, S.ntile);
+            for (int t = 0; t < S.ntile; ++t) b.rtiles[base + t] = S.tile0 + t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *b.rcount = cnt;
 }
 
 // R2: exclusive scan of the occupancy (one 256-thread block per system); resets counts.
@@ -227,18 +343,27 @@ __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
         if (threadIdx.x == 0) carry_s = carry + tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) start[ncells] = carry_s;
+    if (threadIdx.x == 0) {
+        start[ncells] = carry_s;
+        if (carry_s != S.n) atomicOr(&st.err, NEFE_ERR_CELL);
+    }
 }
 
 // R3: scatter atoms into their cell segment (order inside a cell fixed by R4).
-__global__ void __launch_bounds__(kTile) k_cells_fill(Bufs b, int force_all) {
-    const TileAtom ta = tile_of(b, blockIdx.x);
+__device__ void cells_fill_tile(const Bufs& b, int tile) {
+    const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
-    if (!force_all && !b.st[ta.sys].rebuild) return;
     if ((int)threadIdx.x >= ta.count) return;
     const int i = ta.first + threadIdx.x;
     const int pos = atomicAdd(&b.cell_cursor[S.cell0 + b.cell_of[i]], 1);
+    if (pos < 0 || pos >= S.n) {                 // inconsistent occupancy: record, never write out of range
+        atomicOr(&b.st[ta.sys].err, NEFE_ERR_CELL);
+        return;
+    }
     b.perm[S.off + pos] = i;
+}
+__global__ void __launch_bounds__(kTile) k_cells_fill(Bufs b) {
+    NEFE_FOR_TILES(b, cells_fill_tile(b, tile));
 }
 
 // R4: insertion sort of each cell segment by atom index (stable order by (cell, atom)).
@@ -251,7 +376,7 @@ __global__ void __launch_bounds__(256) k_cells_sort(Bufs b, int force_all) {
     const int* start = b.cell_start + S.cell0 + s;
     int* p = b.perm + S.off;
     for (int c = threadIdx.x; c < ncells; c += blockDim.x) {
-        const int lo = start[c], hi = start[c + 1];
+        const int lo = max(0, min(start[c], S.n)), hi = max(lo, min(start[c + 1], S.n));
         for (int a = lo + 1; a < hi; ++a) {
             const int key = p[a];
             int z = a - 1;
@@ -275,78 +400,124 @@ __device__ __forceinline__ bool exact_pair_in(const Bufs& b, const double box[3]
     return rr < rcs2;
 }
 
-// R5: Verlet list of atom i from the 27 cell offsets.  A candidate is accepted or rejected
-// on its mirror distance when that is outside a relative band of 1e-4 (FP32) / 1e-10 (FP64)
-// around rcs^2; inside the band the exact FP64 criterion decides (and must agree with the
-// offset's image), so the list equals the plain definition bit for bit.
+// R5: Verlet list, kListLanes lanes per atom.  The candidates of the 27 neighbour cells
+// (cell offset o in {-1,0,1}^3) are dealt over the lanes; a candidate is accepted or
+// rejected on its mirror distance when that lies outside a relative band of 1e-4 (FP32) /
+// 1e-10 (FP64) around rcs^2, and inside the band by the exact FP64 criterion (which must
+// also agree with the offset's image), so the list equals the plain definition bit for
+// bit.  Accepted entries are ranked by atom index (a rank count, no atomics) into the row.
+constexpr int kListLanes = 8;
+constexpr int kRebuildBlocks = 152 * 8;   // bounded grid of the worklist-driven rebuild kernels
 template <typename T>
-__global__ void __launch_bounds__(kTile) k_nlist(Bufs b, int force_all) {
+__device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap], int (*cstart)[28],
+                           int (*ccell)[27]) {
     using T4 = typename V4<T>::t;
-    const TileAtom ta = tile_of(b, blockIdx.x);
+    constexpr int L = kListLanes, G = kTile / L;
+    const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
-    if (!force_all && !st.rebuild) return;
-    if ((int)threadIdx.x >= ta.count) return;
-    const int i = ta.first + threadIdx.x;
+    const int lane = threadIdx.x % L, grp = threadIdx.x / L;
+    const int lbase = ((threadIdx.x & 31) / L) * L;
+    const unsigned gmask = ((1u << L) - 1u) << lbase;
+    const int ia = part * G + grp;
+    const bool valid = ia < ta.count;
+    const int i = ta.first + ia;
+    if (!valid) return;                          // whole group leaves together
     const int nx = st.ncell[0], ny = st.ncell[1], nz = st.ncell[2];
     const int cell = b.cell_of[i];
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+    const int* start = b.cell_start + S.cell0 + ta.sys;
+    // per-group table of the 27 cells and the prefix of their occupancy
+    if (lane == 0) {
+        int acc = 0;
+        for (int o = 0; o < 27; ++o) {
+            const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+            const int c2 = (cx + ox + nx) % nx + nx * (((cy + oy + ny) % ny) + ny * ((cz + oz + nz) % nz));
+            ccell[grp][o] = c2;
+            cstart[grp][o] = acc;
+            const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
+            acc += hi - lo;
+        }
+        cstart[grp][27] = acc;
+    }
+    __syncwarp(gmask);
+    const int total = cstart[grp][27];
     const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
     const T hx = (T)st.h[0], hy = (T)st.h[1], hz = (T)st.h[2];
     const double rcs2 = __dmul_rn(S.rcs, S.rcs);
     const T band = sizeof(T) == 4 ? (T)1e-4 : (T)1e-10;
     const T lo2 = (T)rcs2 * ((T)1 - band), hi2 = (T)rcs2 * ((T)1 + band);
-    const int* start = b.cell_start + S.cell0 + ta.sys;
-    int row[kMaxCap];
-    int count = 0;
     const int cap = b.cap;
-    for (int oz = -1; oz <= 1; ++oz) {
-        const int czz = (cz + oz + nz) % nz;
-        for (int oy = -1; oy <= 1; ++oy) {
-            const int cyy = (cy + oy + ny) % ny;
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int cxx = (cx + ox + nx) % nx;
-                const int c2 = cxx + nx * (cyy + ny * czz);
-                const int code = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
-                const int pe = start[c2 + 1];
-                for (int p = start[c2]; p < pe; ++p) {
-                    const int j = b.perm[S.off + p];
-                    if (j == i && code == 13) continue;
-                    const T4 xj = reinterpret_cast<const T4*>(b.xs)[j];
-                    const T dx = xj.x - xi.x + (T)ox * hx;
-                    const T dy = xj.y - xi.y + (T)oy * hy;
-                    const T dz = xj.z - xi.z + (T)oz * hz;
-                    const T dd = dx * dx + dy * dy + dz * dz;
-                    bool in;
-                    if (dd < lo2) {
-                        in = true;
-                    } else if (dd > hi2) {
-                        in = false;
-                    } else {
-                        double d[3];
-                        in = exact_pair_in(b, st.box, i, j, rcs2, d);
-                        // the exact (minimum) image must be the one reached through this offset
-                        in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
-                             fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
-                             fabs(d[2] - (double)dz) < 0.5 * st.h[2];
-                    }
-                    if (!in) continue;
-                    if (count < cap) {
-                        const int e = j | (code << kCodeShift);
-                        int z = count;
-                        while (z > 0 && (row[z - 1] & (int)kIndexMask) > j) { row[z] = row[z - 1]; --z; }
-                        row[z] = e;
-                    }
-                    ++count;
+    int count = 0;
+    int o = 0;
+    for (int base = 0; base < total; base += L) {
+        const int f = base + lane;
+        bool in = false;
+        int e = 0;
+        if (f < total) {
+            while (f >= cstart[grp][o + 1]) ++o;
+            const int c2 = ccell[grp][o];
+            const int j = b.perm[S.off + max(0, min(start[c2], S.n)) + (f - cstart[grp][o])];
+            const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+            if (j < S.off || j >= S.off + S.n) {
+                atomicOr(&st.err, NEFE_ERR_CELL);
+            } else if (!(j == i && o == 13)) {
+                const T4 xj = reinterpret_cast<const T4*>(b.xs)[j];
+                const T dx = xj.x - xi.x + (T)ox * hx;
+                const T dy = xj.y - xi.y + (T)oy * hy;
+                const T dz = xj.z - xi.z + (T)oz * hz;
+                const T dd = dx * dx + dy * dy + dz * dz;
+                if (dd < lo2) {
+                    in = true;
+                } else if (dd <= hi2) {
+                    double d[3];
+                    in = exact_pair_in(b, st.box, i, j, rcs2, d);
+                    in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
+                         fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
+                         fabs(d[2] - (double)dz) < 0.5 * st.h[2];
                 }
+                e = j | (o << kCodeShift);
             }
         }
+        const unsigned bal = __ballot_sync(gmask, in);
+        if (in) {
+            const int pos = count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+            if (pos < kMaxCap) buf[grp][pos] = e;
+        }
+        count += __popc(bal);
     }
-    int* out = b.nbr + (size_t)i * cap;
+    __syncwarp(gmask);
+    // rank by atom index into the row (indices in a row are distinct)
     const int m = count < cap ? count : cap;
-    for (int z = 0; z < m; ++z) out[z] = row[z];
-    b.cnt[i] = count;
-    if (count > cap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
+    const int have = count < kMaxCap ? count : kMaxCap;
+    int* out = b.nbr + (size_t)i * cap;
+    for (int a = lane; a < have; a += L) {
+        const int e = buf[grp][a];
+        const int key = e & (int)kIndexMask;
+        int r = 0;
+        for (int z = 0; z < have; ++z) r += ((buf[grp][z] & (int)kIndexMask) < key) ? 1 : 0;
+        if (r < m) out[r] = e;
+    }
+    if (lane == 0) {
+        b.cnt[i] = count;
+        if (count > cap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
+    }
+    __syncwarp(gmask);                           // shared tables reused by the next item
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_nlist(Bufs b) {
+    constexpr int L = kListLanes, G = kTile / L;
+    __shared__ int buf[G][kMaxCap];
+    __shared__ int cstart[G][28];
+    __shared__ int ccell[G][27];
+    if (b.rtiles) {
+        const int n = *b.rcount * L;
+        for (int w = blockIdx.x; w < n; w += gridDim.x)
+            nlist_item<T>(b, b.rtiles[w / L], w % L, buf, cstart, ccell);
+    } else {
+        nlist_item<T>(b, blockIdx.x / L, blockIdx.x % L, buf, cstart, ccell);
+    }
 }
 
 // Mirror only (stateless forces): same q / xs formula as R1, without counting.
@@ -360,8 +531,10 @@ __global__ void __launch_bounds__(kTile) k_mirror(Bufs b) {
     grid_for(st.box, S.rcs, S.ncell_cap, n3);
     double h[3];
     for (int k = 0; k < 3; ++k) h[k] = __ddiv_rn(st.box[k], (double)n3[k]);
-    if (blockIdx.x == S.tile0 && threadIdx.x == 0)
+    if (blockIdx.x == S.tile0 && threadIdx.x == 0) {
         for (int k = 0; k < 3; ++k) { st.ncell[k] = n3[k]; st.h[k] = h[k]; st.hb[k] = h[k]; }
+        refresh_box_f(st);
+    }
     if ((int)threadIdx.x >= ta.count) return;
     const int i = ta.first + threadIdx.x;
     double xs[3];
@@ -380,8 +553,26 @@ __global__ void __launch_bounds__(kTile) k_mirror(Bufs b) {
 }
 
 // ------------------------------------------------------------------------------------
-// Half kick + drift.  mode 0 (setup): mirror and noise sums only.
+// Half kick + drift.  mode 0 (setup): mirror and noise only.
+// x = anchor + dhi + dlo; per step the displacement grows by dt phi v + (s - 1) x (affine
+// box drift).  In the FP32 path (dhi, dlo) is a compensated pair: a two-sum keeps the
+// rounding error of every increment in dlo.
 // ------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void comp_add(T& hi, T& lo, T d) {
+    if constexpr (sizeof(T) == 8) {
+        hi += d;
+    } else {
+        const T s = hi + d;
+        const T bp = s - hi;
+        const T err = (hi - (s - bp)) + (d - bp);
+        lo += err;
+        const T h2 = s + lo;
+        lo = lo - (h2 - s);
+        hi = h2;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
     using T4 = typename V4<T>::t;
@@ -392,28 +583,53 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
     if ((int)threadIdx.x < ta.count) {
         const int i = ta.first + threadIdx.x;
         const size_t N = b.ntot;
-        double xv[3] = {b.x[i], b.x[N + i], b.x[2 * N + i]};
-        if (mode == 1) {
-            double vv[3] = {b.v[i], b.v[N + i], b.v[2 * N + i]};
-            const T4 F = reinterpret_cast<const T4*>(b.F)[i];
-            const double c = 0.5 * b.dt / S.mass_e;
-            vv[0] += c * (double)F.x; vv[1] += c * (double)F.y; vv[2] += c * (double)F.z;
-            for (int k = 0; k < 3; ++k) xv[k] = st.s[k] * xv[k] + (b.dt * st.phi[k]) * vv[k];
-            for (int k = 0; k < 3; ++k) { b.v[k * N + i] = vv[k]; b.x[k * N + i] = xv[k]; }
+        T* V = reinterpret_cast<T*>(b.v);
+        T* DH = reinterpret_cast<T*>(b.dhi);
+        T* DL = reinterpret_cast<T*>(b.dlo);
+        const T4 xa = reinterpret_cast<const T4*>(b.xa)[i];
+        const T xav[3] = {xa.x, xa.y, xa.z};
+        const bool scaled = st.scaled != 0, hmoved = st.hmoved != 0;
+        int4 q = make_int4(0, 0, 0, 0);
+        if (scaled || hmoved) q = b.q[i];
+        const int qa[3] = {q.x, q.y, q.z};
+        T dh[3], dl[3];
+        for (int k = 0; k < 3; ++k) {
+            dh[k] = DH[k * N + i];
+            if constexpr (sizeof(T) == 4) dl[k] = DL[k * N + i]; else dl[k] = (T)0;
         }
-        const int4 q = b.q[i];
-        const double m0 = xv[0] - (double)q.x * st.h[0];
-        const double m1 = xv[1] - (double)q.y * st.h[1];
-        const double m2 = xv[2] - (double)q.z * st.h[2];
-        const T4 m = mk4((T)m0, (T)m1, (T)m2, (T)0);
-        reinterpret_cast<T4*>(b.xs)[i] = m;
-        const T4 mb = reinterpret_cast<const T4*>(b.xsb)[i];
-        const T r0 = (T)(st.h[0] / st.hb[0]), r1 = (T)(st.h[1] / st.hb[1]), r2 = (T)(st.h[2] / st.hb[2]);
-        const T d0 = m.x - mb.x * r0, d1 = m.y - mb.y * r1, d2 = m.z - mb.z * r2;
-        if ((double)(d0 * d0 + d1 * d1 + d2 * d2) > st.thr2 && !st.rebuild) atomicOr(&st.rebuild, 1);
-        if (S.tdamp > 0.0) {
+        if (mode == 1) {
+            const T4 F = reinterpret_cast<const T4*>(b.F)[i];
+            const T fv[3] = {F.x, F.y, F.z};
+            const T ck = pick<T>(S.ckick, S.ckick_f), dt = pick<T>(b.dt, S.dt_f);
+            for (int k = 0; k < 3; ++k) {
+                const T vk = V[k * N + i] + ck * fv[k];
+                V[k * N + i] = vk;
+                T d = dt * pick<T>(st.phi[k], st.phi_f[k]) * vk;
+                if (scaled) {   // (s - 1) x with x = xa + q hb + displacement
+                    const T xk = xav[k] + (T)qa[k] * pick<T>(st.hb[k], st.hb_f[k]) + dh[k];
+                    d += pick<T>(st.s[k] - 1.0, st.sm1_f[k]) * xk;
+                }
+                comp_add<T>(dh[k], dl[k], d);
+                DH[k * N + i] = dh[k];
+                if constexpr (sizeof(T) == 4) DL[k * N + i] = dl[k];
+            }
+        }
+        T m[3];
+        for (int k = 0; k < 3; ++k) {
+            m[k] = xav[k] + (dh[k] + dl[k]);
+            if (hmoved) m[k] -= (T)qa[k] * (pick<T>(st.h[k], st.h_f[k]) - pick<T>(st.hb[k], st.hb_f[k]));
+        }
+        reinterpret_cast<T4*>(b.xs)[i] = mk4(m[0], m[1], m[2], (T)0);
+        T dd2 = 0;
+        for (int k = 0; k < 3; ++k) {
+            const T dd = hmoved ? m[k] - xav[k] * pick<T>(st.h[k] / st.hb[k], st.rho_f[k]) : dh[k] + dl[k];
+            dd2 += dd * dd;
+        }
+        if (dd2 > pick<T>(st.thr2, st.thr2_f) && !st.rebuild) atomicOr(&st.rebuild, 1);
+        if (S.thermo) {
             T z[3];
             Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)st.k, (uint64_t)(i - S.off), z);
+            reinterpret_cast<T4*>(b.xi)[i] = mk4(z[0], z[1], z[2], (T)0);
             xs_sum[0] = z[0]; xs_sum[1] = z[1]; xs_sum[2] = z[2];
         }
     }
@@ -421,100 +637,106 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
 }
 
 // ------------------------------------------------------------------------------------
-// Stillinger-Weber force kernel: L lanes per atom, 128/L atoms per block.
+// Stillinger-Weber terms for one edge of length r (A):
+//   phi = eps A (B s^-p - s^-q) exp(1/(s - a)),  g = exp(gamma/(s - a)),  s = r/sigma,
+// with dphi/dr and dg/dr.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned lanemask_lt() {
-    return (1u << (threadIdx.x & 31)) - 1u;
-}
+// Distance (in sigma) below the cutoff a inside which an edge is treated as cut off: there
+// exp(1/(s - a)) and exp(gamma/(s - a)) underflow to 0 anyway, and 1/(s - a) would overflow
+// (0 * inf = NaN) when s rounds onto a.
+template <typename T> __device__ __forceinline__ T cut_eps() { return sizeof(T) == 4 ? (T)1e-5 : (T)1e-12; }
 
 template <typename T>
 __device__ __forceinline__ void sw_edge(const SWc<T>& P, T r, T& phi, T& dphi, T& g, T& dg) {
     const T s = r * P.inv_sig;
-    const T id = (T)1 / (s - P.a);
-    const T e1 = exp(id);
-    g = exp(P.gam * id);
+    if (!(s - P.a < -cut_eps<T>())) {
+        phi = dphi = g = dg = (T)0;
+        return;
+    }
+    const T id = xrcp(s - P.a);
+    const T e1 = xexp(id);
+    g = xexp(P.gam * id);
     T rp, rq;
     if (P.int_pq) {
-        const T is2 = (T)1 / (s * s);
+        const T is2 = xrcp(s * s);
         rp = is2 * is2;
         rq = (T)1;
     } else {
-        rp = pow(s, -P.p);
-        rq = pow(s, -P.q);
+        rp = xpow(s, -P.p);
+        rq = xpow(s, -P.q);
     }
     const T poly = P.B * rp - rq;
     phi = P.epsA * poly * e1;
-    dphi = P.epsA * e1 * ((-P.p * P.B * rp + P.q * rq) / s - poly * id * id) * P.inv_sig;
+    dphi = P.epsA * e1 * ((-P.p * P.B * rp + P.q * rq) * xrcp(s) - poly * id * id) * P.inv_sig;
     dg = -g * P.gam * id * id * P.inv_sig;
 }
 
-template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(kTile) k_force(Bufs b) {
+// Force pass A.  L lanes per atom, 128/L atoms per block, the in-cutoff shell staged in
+// shared memory and also stored compactly (d_ij and g_ij per entry, neighbour index) for
+// pass B.  Pair terms on the lanes that find the edge; triplets (i; a, b), a < b, dealt
+// over the lanes.  Writes the atom's force from these terms (P.xyz) and its energy (P.w:
+// half of each pair term, every triplet centred on it); block sums of energy and virial.
+template <typename T, int L>
+__global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int G = kTile / L;
     __shared__ T4 sh_d[G][kShell];
     __shared__ T sh_g[G][kShell];
     __shared__ T sh_dg[G][kShell];
-    __shared__ int sh_e[G][kShell];
 
-    const int tile = blockIdx.x / L, part = blockIdx.x % L;
+    const int tile = blockIdx.x / L + b.tile_base, part = blockIdx.x % L;
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
+    if (S.pot != POT_SW) return;                 // uniform over the block
     const SWc<T> P = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
-    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (((threadIdx.x & 31) / L) * L));
-    const T hx = (T)st.h[0], hy = (T)st.h[1], hz = (T)st.h[2];
+    const int lbase = ((threadIdx.x & 31) / L) * L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
+    __shared__ T4 soff[27];
+    offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
     const int ia = part * G + grp;
     const bool valid = ia < ta.count;
     const int i = ta.first + ia;
-    // per-system mean of this step's thermostat noise (sum of the 32 slots, once per block)
-    __shared__ T s_xm[3];
-    if (MODE != FM_FORCES && threadIdx.x < 3) {
-        const long long* acc = b.acc + (size_t)ta.sys * ACC_N * kSlots + (size_t)(ACC_XI + threadIdx.x) * kSlots;
-        long long sum = 0;
-        for (int sl = 0; sl < kSlots; ++sl) sum += acc[sl];
-        s_xm[threadIdx.x] = (T)((double)sum / kFix / (double)S.n);
-    }
-    __syncthreads();
 
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-    bool shell_ovf = false;
-    if (valid && S.pot == POT_SW) {
+    if (valid) {
         const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
         const int ci = min(b.cnt[i], b.cap);
         const int* row = b.nbr + (size_t)i * b.cap;
+        T4* Sd = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
+        int* Sj = b.shj + (size_t)i * kShell;
         int m = 0;
-        // phase 1: in-cutoff shell of i, pair terms
         for (int base = 0; base < ci; base += L) {
             const int sidx = base + lane;
             bool in = false;
             T dx = 0, dy = 0, dz = 0, r2 = 0;
-            int e = 0;
+            int j = 0;
             if (sidx < ci) {
-                e = row[sidx];
-                const int j = e & (int)kIndexMask;
-                const int code = (int)((unsigned)e >> kCodeShift);
+                const int e = row[sidx];
+                j = e & (int)kIndexMask;
+                const T4 oh = soff[(unsigned)e >> kCodeShift];
                 const T4 xj = reinterpret_cast<const T4*>(b.xs)[j];
-                dx = xj.x - xi.x + (T)(code % 3 - 1) * hx;
-                dy = xj.y - xi.y + (T)((code / 3) % 3 - 1) * hy;
-                dz = xj.z - xi.z + (T)(code / 9 - 1) * hz;
+                dx = (xj.x - xi.x) + oh.x;
+                dy = (xj.y - xi.y) + oh.y;
+                dz = (xj.z - xi.z) + oh.z;
                 r2 = dx * dx + dy * dy + dz * dz;
                 in = r2 < P.rc2;
             }
             const unsigned bal = __ballot_sync(gmask, in);
             if (in) {
-                const int pos = m + __popc(bal & lanemask_lt());
+                const int pos = m + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
                 if (pos < kShell) {
-                    const T r = sqrt(r2);
+                    const T r = r2 * xrsqrt(r2);
                     T phi, dphi, g, dg;
                     sw_edge<T>(P, r, phi, dphi, g, dg);
                     sh_d[grp][pos] = mk4(dx, dy, dz, r);
                     sh_g[grp][pos] = g;
                     sh_dg[grp][pos] = dg;
-                    sh_e[grp][pos] = e;
-                    const T c = dphi / r;
+                    Sd[pos] = mk4(dx, dy, dz, g);
+                    Sj[pos] = j;
+                    const T c = dphi * xrcp(r);
                     fx += c * dx; fy += c * dy; fz += c * dz;
                     en += (T)0.5 * phi;
                     const T hc = (T)-0.5 * c;
@@ -524,29 +746,30 @@ __global__ void __launch_bounds__(kTile) k_force(Bufs b) {
             }
             m += __popc(bal);
         }
-        if (m > kShell) { shell_ovf = true; m = kShell; }
+        if (m > kShell) {
+            if (lane == 0) atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
+            m = kShell;
+        }
         __syncwarp(gmask);
-        // phase 2: triplets centred at i, pairs (a < b) of the shell, flat index dealt mod L
+        // triplets centred at i: pairs (a < b) of the shell, flat index dealt mod L
         int t0 = 0;
         for (int a = 0; a < m - 1; ++a) {
             const int rowlen = m - 1 - a;
-            int off = (lane - t0) % L;
-            if (off < 0) off += L;
+            const int off = (lane - t0) & (L - 1);
             if (off < rowlen) {
                 const T4 da = sh_d[grp][a];
                 const T ga = sh_g[grp][a], dga = sh_dg[grp][a];
-                const T ira = (T)1 / da.w;
+                const T ira = xrcp(da.w);
                 const T uax = da.x * ira, uay = da.y * ira, uaz = da.z * ira;
                 for (int bb = a + 1 + off; bb < m; bb += L) {
                     const T4 db = sh_d[grp][bb];
                     const T gb = sh_g[grp][bb], dgb = sh_dg[grp][bb];
-                    const T irb = (T)1 / db.w;
+                    const T irb = xrcp(db.w);
                     const T ubx = db.x * irb, uby = db.y * irb, ubz = db.z * irb;
                     const T c = uax * ubx + uay * uby + uaz * ubz;
                     const T dc = c - P.c0;
                     const T two = (T)2 * P.epslam * dc * ga * gb;
                     const T dc2 = P.epslam * dc * dc;
-                    // f_a = -dh/dx_a, f_b = -dh/dx_b
                     const T ta_ = two * ira, tb_ = two * irb;
                     const T fax = -(ta_ * (ubx - c * uax) + dc2 * dga * gb * uax);
                     const T fay = -(ta_ * (uby - c * uay) + dc2 * dga * gb * uay);
@@ -566,112 +789,200 @@ __global__ void __launch_bounds__(kTile) k_force(Bufs b) {
             }
             t0 += rowlen;
         }
-        // phase 3: triplets centred at each shell neighbour j in which i is a leg
-        for (int a = 0; a < m; ++a) {
-            const int ea = sh_e[grp][a];
-            const int j = ea & (int)kIndexMask;
-            const T4 da = sh_d[grp][a];
-            const T ga = sh_g[grp][a], dga = sh_dg[grp][a];
-            const T rji = da.w, irji = (T)1 / rji;
-            const T ux = -da.x * irji, uy = -da.y * irji, uz = -da.z * irji;   // unit j -> i
-            const T4 xj = reinterpret_cast<const T4*>(b.xs)[j];
-            const int cj = min(b.cnt[j], b.cap);
-            const int* rowj = b.nbr + (size_t)j * b.cap;
-            for (int sidx = lane; sidx < cj; sidx += L) {
-                const int e = rowj[sidx];
-                const int k = e & (int)kIndexMask;
-                if (k == i) continue;
-                const int code = (int)((unsigned)e >> kCodeShift);
-                const T4 xk = reinterpret_cast<const T4*>(b.xs)[k];
-                const T dx = xk.x - xj.x + (T)(code % 3 - 1) * hx;
-                const T dy = xk.y - xj.y + (T)((code / 3) % 3 - 1) * hy;
-                const T dz = xk.z - xj.z + (T)(code / 9 - 1) * hz;
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (!(r2 < P.rc2)) continue;
-                const T rk = sqrt(r2), irk = (T)1 / rk;
-                const T gk = exp(P.gam / (rk * P.inv_sig - P.a));
-                const T vx = dx * irk, vy = dy * irk, vz = dz * irk;
-                const T c = ux * vx + uy * vy + uz * vz;
-                const T dc = c - P.c0;
-                const T two = (T)2 * P.epslam * dc * ga * gk * irji;
-                const T dc2 = P.epslam * dc * dc * dga * gk;
-                fx -= two * (vx - c * ux) + dc2 * ux;
-                fy -= two * (vy - c * uy) + dc2 * uy;
-                fz -= two * (vz - c * uz) + dc2 * uz;
-            }
-        }
-        // group reduction
+        T e_own = en;
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) {
             fx += __shfl_xor_sync(gmask, fx, o);
             fy += __shfl_xor_sync(gmask, fy, o);
             fz += __shfl_xor_sync(gmask, fz, o);
-            en += __shfl_xor_sync(gmask, en, o);
-            w0 += __shfl_xor_sync(gmask, w0, o);
-            w1 += __shfl_xor_sync(gmask, w1, o);
-            w2 += __shfl_xor_sync(gmask, w2, o);
-            w3 += __shfl_xor_sync(gmask, w3, o);
-            w4 += __shfl_xor_sync(gmask, w4, o);
-            w5 += __shfl_xor_sync(gmask, w5, o);
+            e_own += __shfl_xor_sync(gmask, e_own, o);
+        }
+        if (lane == 0) {
+            reinterpret_cast<T4*>(b.P)[i] = mk4(fx, fy, fz, e_own);
+            b.shn[i] = m;
         }
     }
-    if (shell_ovf && lane == 0) atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
+    T red[8] = {en, (T)0, w0, w1, w2, w3, w4, w5};
+    block_sum_to_acc<T, 8>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+}
 
+// Force pass B, one thread per atom:
+//   F_SW(i) = P(i) + sum_{j in shell(i)} sum_{k in shell(j), k != i} -d h(j; i, k) / d x_i
+// from the stored shells (d_ji = -d_ij, g_ji = g_ij; d_jk, g_jk from j's shell).  Then, in
+// FM_SETUP / FM_STEP: Einstein springs, lambda mixing, Langevin force (this step's noise with
+// its per-system mean removed), second half kick and the kinetic sums.
+constexpr int kGatherLanes = 4;
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
+    using T4 = typename V4<T>::t;
+    constexpr int L = kGatherLanes, G = kTile / L;
+    const int tile = blockIdx.x / L + b.tile_base, part = blockIdx.x % L;
+    const TileAtom ta = tile_of(b, tile);
+    const DevSys& S = b.sys[ta.sys];
+    DevState& st = b.st[ta.sys];
+    __shared__ T s_xm[3];
+    if (MODE != FM_FORCES && threadIdx.x < 3) {
+        const long long* acc = b.acc + (size_t)ta.sys * ACC_N * kSlots + (size_t)(ACC_XI + threadIdx.x) * kSlots;
+        long long sum = 0;
+        for (int sl = 0; sl < kSlots; ++sl) sum += acc[sl];
+        if constexpr (sizeof(T) == 4) {   // sum 2^-32 / n from its 32-bit halves, FP32 only
+            const float hi = (float)(int)(sum >> 32);
+            const float lo = (float)(unsigned)(sum & 0xffffffffLL) * 0x1p-32f;
+            s_xm[threadIdx.x] = (hi + lo) * S.inv_n_f;
+        } else {
+            s_xm[threadIdx.x] = (T)((double)sum / kFix / (double)S.n);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x % L, grp = threadIdx.x / L;
+    const int lbase = ((threadIdx.x & 31) / L) * L;
+    const unsigned gmask = ((1u << L) - 1u) << lbase;
+    const int ia = part * G + grp;
     T red[14];
 #pragma unroll
     for (int k = 0; k < 14; ++k) red[k] = (T)0;
-    if (valid && lane == 0) {
+    if (ia < ta.count) {
+        const int i = ta.first + ia;
         const size_t N = b.ntot;
-        T fint[3] = {fx, fy, fz};
-        T u_int = en, u_ref = 0;
-        T fe[3] = {(T)0, (T)0, (T)0};
-        if (MODE == FM_FORCES) {
-            b.f_out[i] = (double)fint[0]; b.f_out[N + i] = (double)fint[1]; b.f_out[2 * N + i] = (double)fint[2];
-            if (b.e_atom) b.e_atom[i] = (double)u_int;
-        } else {
-            if (S.pot == POT_EINSTEIN || S.k_E > 0.0) {
-                // spring displacement from FP64 positions; energies in FP64
-                double d[3];
-                for (int k = 0; k < 3; ++k) d[k] = b.x[k * N + i] - b.r0[k * N + i];
-                const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                if (S.pot == POT_EINSTEIN) {
-                    u_int = (T)(0.5 * S.k_int * d2);
-                    for (int k = 0; k < 3; ++k) fint[k] = (T)(-S.k_int) * (T)d[k];
+        T f[3] = {(T)0, (T)0, (T)0}, e_i = 0;
+        if (S.pot == POT_SW) {
+            const SWc<T> Pc = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
+            const T4* Sd = reinterpret_cast<const T4*>(b.shd);
+            const int m = b.shn[i];
+            // lanes share the atom's shell entries a; each walks the shell of neighbour j
+            for (int a = lane; a < m; a += L) {
+                const T4 dij = Sd[(size_t)i * kShell + a];
+                const int j = b.shj[(size_t)i * kShell + a];
+                const T r2 = dij.x * dij.x + dij.y * dij.y + dij.z * dij.z;
+                const T irji = xrsqrt(r2), rji = r2 * irji;
+                const T ux = -dij.x * irji, uy = -dij.y * irji, uz = -dij.z * irji;   // unit j -> i
+                const T gji = dij.w;
+                const T den = rji * Pc.inv_sig - Pc.a;
+                const T idn = den < -cut_eps<T>() ? xrcp(den) : (T)0;
+                const T dgji = -gji * Pc.gam * idn * idn * Pc.inv_sig;
+                const int mj = b.shn[j];
+                const T4* Sdj = Sd + (size_t)j * kShell;
+                const int* Sjj = b.shj + (size_t)j * kShell;
+                for (int t = 0; t < mj; ++t) {
+                    const T4 djk = Sdj[t];
+                    if (Sjj[t] == i) continue;
+                    const T rk2 = djk.x * djk.x + djk.y * djk.y + djk.z * djk.z;
+                    const T irk = xrsqrt(rk2);
+                    const T vx = djk.x * irk, vy = djk.y * irk, vz = djk.z * irk;
+                    const T gk = djk.w;
+                    const T c = ux * vx + uy * vy + uz * vz;
+                    const T dc = c - Pc.c0;
+                    const T two = (T)2 * Pc.epslam * dc * gji * gk * irji;
+                    const T dc2 = Pc.epslam * dc * dc * dgji * gk;
+                    f[0] -= two * (vx - c * ux) + dc2 * ux;
+                    f[1] -= two * (vy - c * uy) + dc2 * uy;
+                    f[2] -= two * (vz - c * uz) + dc2 * uz;
                 }
-                if (S.k_E > 0.0) {
-                    u_ref = (T)(0.5 * S.k_E * d2);
-                    for (int k = 0; k < 3; ++k) fe[k] = (T)(-S.k_E) * (T)d[k];
-                }
             }
-            double v[3] = {b.v[i], b.v[N + i], b.v[2 * N + i]};
-            const T si = (T)st.scale_int, se = (T)st.scale_E;
-            T F[3];
-            for (int k = 0; k < 3; ++k) F[k] = si * fint[k] + se * fe[k];
-            if (S.tdamp > 0.0) {
-                T z[3];
-                Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)st.k, (uint64_t)(i - S.off), z);
-                const T amp = (T)S.amp, gam = (T)S.gam;
-                for (int k = 0; k < 3; ++k) F[k] += -gam * (T)v[k] + amp * (z[k] - s_xm[k]);
+#pragma unroll
+            for (int o = L / 2; o > 0; o >>= 1) {
+                f[0] += __shfl_xor_sync(gmask, f[0], o);
+                f[1] += __shfl_xor_sync(gmask, f[1], o);
+                f[2] += __shfl_xor_sync(gmask, f[2], o);
             }
-            if (MODE == FM_STEP) {
-                for (int k = 0; k < 3; ++k) { v[k] += S.ckick * (double)F[k]; b.v[k * N + i] = v[k]; }
-            }
-            reinterpret_cast<T4*>(b.F)[i] = mk4(F[0], F[1], F[2], (T)0);
-            const T me = (T)S.mass_e;
-            const T vx = (T)v[0], vy = (T)v[1], vz = (T)v[2];
-            red[8] = me * vx * vx;
-            red[9] = me * vy * vy;
-            red[10] = me * vz * vz;
-            red[11] = me * vx * vy;
-            red[12] = me * vx * vz;
-            red[13] = me * vy * vz;
+            const T4 p = reinterpret_cast<const T4*>(b.P)[i];
+            f[0] += p.x; f[1] += p.y; f[2] += p.z; e_i = p.w;
         }
-        red[0] = u_int;
-        red[1] = u_ref;
-        red[2] = w0; red[3] = w1; red[4] = w2;
-        red[5] = w3; red[6] = w4; red[7] = w5;
+        if (lane == 0) {
+            if (MODE == FM_FORCES) {
+                b.f_out[i] = (double)f[0]; b.f_out[N + i] = (double)f[1]; b.f_out[2 * N + i] = (double)f[2];
+                if (b.e_atom) b.e_atom[i] = (double)e_i;
+            } else {
+                T fint[3] = {f[0], f[1], f[2]}, fe[3] = {(T)0, (T)0, (T)0};
+                T u_int = 0, u_ref = 0;
+                if (S.springs) {
+                    const T4 d0 = reinterpret_cast<const T4*>(b.sd0)[i];
+                    const T* DH = reinterpret_cast<const T*>(b.dhi);
+                    const T* DL = reinterpret_cast<const T*>(b.dlo);
+                    T d[3] = {d0.x, d0.y, d0.z};
+                    for (int k = 0; k < 3; ++k) {
+                        d[k] += DH[k * N + i];
+                        if constexpr (sizeof(T) == 4) d[k] += DL[k * N + i];
+                    }
+                    const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (S.pot == POT_EINSTEIN) {
+                        const T k_i = pick<T>(S.k_int, S.kint_f);
+                        u_int = (T)0.5 * k_i * d2;
+                        for (int k = 0; k < 3; ++k) fint[k] = -k_i * d[k];
+                    }
+                    const T k_e = pick<T>(S.k_E, S.kE_f);
+                    u_ref = (T)0.5 * k_e * d2;
+                    for (int k = 0; k < 3; ++k) fe[k] = -k_e * d[k];
+                }
+                T* V = reinterpret_cast<T*>(b.v);
+                T v[3] = {V[i], V[N + i], V[2 * N + i]};
+                const T si = pick<T>(st.scale_int, st.scale_int_f), se = pick<T>(st.scale_E, st.scale_E_f);
+                T F[3];
+                for (int k = 0; k < 3; ++k) F[k] = si * fint[k] + se * fe[k];
+                if (S.thermo) {
+                    const T4 z = reinterpret_cast<const T4*>(b.xi)[i];
+                    const T zz[3] = {z.x, z.y, z.z};
+                    const T amp = pick<T>(S.amp, S.amp_f), gam = pick<T>(S.gam, S.gam_f);
+                    for (int k = 0; k < 3; ++k) F[k] += -gam * v[k] + amp * (zz[k] - s_xm[k]);
+                }
+                if (MODE == FM_STEP) {
+                    const T ck = pick<T>(S.ckick, S.ckick_f);
+                    for (int k = 0; k < 3; ++k) { v[k] += ck * F[k]; V[k * N + i] = v[k]; }
+                }
+                reinterpret_cast<T4*>(b.F)[i] = mk4(F[0], F[1], F[2], (T)0);
+                const T me = pick<T>(S.mass_e, S.mass_f);
+                red[0] = u_int;
+                red[1] = u_ref;
+                red[8] = me * v[0] * v[0];
+                red[9] = me * v[1] * v[1];
+                red[10] = me * v[2] * v[2];
+                red[11] = me * v[0] * v[1];
+                red[12] = me * v[0] * v[2];
+                red[13] = me * v[1] * v[2];
+            }
+        }
     }
-    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    if (MODE != FM_FORCES)
+        block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+}
+
+// FP64 positions and velocities for output, and replacement from FP64 input.
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_materialize(Bufs b, double* x, double* v) {
+    const TileAtom ta = tile_of(b, blockIdx.x);
+    if ((int)threadIdx.x >= ta.count) return;
+    const int i = ta.first + threadIdx.x;
+    const size_t N = b.ntot;
+    const T* DH = reinterpret_cast<const T*>(b.dhi);
+    const T* DL = reinterpret_cast<const T*>(b.dlo);
+    const T* V = reinterpret_cast<const T*>(b.v);
+    for (int k = 0; k < 3; ++k) {
+        if (x) {
+            double d = (double)DH[k * N + i];
+            if constexpr (sizeof(T) == 4) d += (double)DL[k * N + i];
+            x[k * N + i] = b.x[k * N + i] + d;
+        }
+        if (v) v[k * N + i] = (double)V[k * N + i];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_inject(Bufs b, const double* x, const double* v) {
+    const TileAtom ta = tile_of(b, blockIdx.x);
+    if ((int)threadIdx.x >= ta.count) return;
+    const int i = ta.first + threadIdx.x;
+    const size_t N = b.ntot;
+    T* DH = reinterpret_cast<T*>(b.dhi);
+    T* DL = reinterpret_cast<T*>(b.dlo);
+    T* V = reinterpret_cast<T*>(b.v);
+    for (int k = 0; k < 3; ++k) {
+        if (x) {
+            b.x[k * N + i] = x[k * N + i];
+            DH[k * N + i] = (T)0;
+            if constexpr (sizeof(T) == 4) DL[k * N + i] = (T)0;
+        }
+        if (v) V[k * N + i] = (T)v[k * N + i];
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -692,11 +1003,16 @@ __device__ double sched_lambda(const DevSys& S, long long k) {
     }
 }
 
-__device__ void force_scales(const DevSys& S, double lam, double& s_int, double& s_e) {
-    if (S.sched == SCHED_FL) { s_int = 1.0 - lam; s_e = lam; }
-    else if (S.sched == SCHED_RS || S.pair >= 0) { s_int = lam; s_e = 0.0; }
+__device__ void force_scales(const DevSys& S, DevState& st) {
+    double s_int, s_e;
+    if (S.sched == SCHED_FL) { s_int = 1.0 - st.lam; s_e = st.lam; }
+    else if (S.sched == SCHED_RS || S.pair >= 0) { s_int = st.lam; s_e = 0.0; }
     else if (S.sched == SCHED_NONE) { s_int = S.lam0; s_e = 0.0; }
     else { s_int = 1.0; s_e = 0.0; }
+    st.scale_int = s_int;
+    st.scale_E = s_e;
+    st.scale_int_f = (float)s_int;
+    st.scale_E_f = (float)s_e;
 }
 
 __device__ double target_pressure(const DevSys& S, const DevState& st) {
@@ -710,7 +1026,6 @@ __device__ void observe(const DevSys& S, DevState& st) {
     const double V = st.box[0] * st.box[1] * st.box[2];
     const double K = 0.5 * (st.kt[0] + st.kt[1] + st.kt[2]);
     for (int k = 0; k < 6; ++k) st.P[k] = (st.kt[k] + st.scale_int * st.vir[k]) / V;
-    const double P = (st.P[0] + st.P[1] + st.P[2]) / 3.0;
     double dhdl = 0.0, H;
     if (S.sched == SCHED_FL) {
         dhdl = st.u_ref - st.u_int;
@@ -727,7 +1042,6 @@ __device__ void observe(const DevSys& S, DevState& st) {
     st.V = V;
     st.dHdl = dhdl;
     st.H = H;
-    (void)P;
 }
 
 __device__ void record_and_kick(const DevSys& S, DevState& st, double dt, double* trace) {
@@ -753,18 +1067,25 @@ __device__ void record_and_kick(const DevSys& S, DevState& st, double dt, double
 }
 
 __device__ void prepare_step(const DevSys& S, DevState& st, double dt) {
-    force_scales(S, st.lam, st.scale_int, st.scale_E);
+    force_scales(S, st);
     double maxrel = 0.0;
+    bool scaled = false;
     for (int k = 0; k < 3; ++k) {
         const double z = st.eta[k] * dt;
         st.s[k] = exp(z);
         st.phi[k] = (z != 0.0) ? expm1(z) / z : 1.0;
+        st.phi_f[k] = (float)st.phi[k];
+        st.sm1_f[k] = (float)(st.s[k] - 1.0);
+        scaled = scaled || (st.s[k] != 1.0);
         st.box[k] *= st.s[k];
         st.h[k] = st.box[k] / (double)st.ncell[k];
         maxrel = fmax(maxrel, fabs(st.h[k] / st.hb[k] - 1.0));
     }
+    st.scaled = scaled ? 1 : 0;
+    refresh_box_f(st);
     const double thr = 0.5 * (S.skin - maxrel * S.rcs);
     st.thr2 = thr > 0.0 ? thr * thr : -1.0;
+    st.thr2_f = (float)st.thr2;
 }
 
 __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups, int mode) {
@@ -777,7 +1098,7 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
             const int s = members[mi];
             DevState& st = b.st[s];
             const long long* acc = b.acc + (size_t)s * ACC_N * kSlots;
-            if (threadIdx.x < ACC_N && threadIdx.x < ACC_XI) {
+            if (threadIdx.x < ACC_XI) {
                 long long sum = 0;
                 for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)threadIdx.x * kSlots + sl];
                 const double v = (double)sum / kFix;
@@ -803,8 +1124,11 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
                 } else if (S.sched != SCHED_NONE) {
                     st.lam = sched_lambda(S, st.k);
                 }
-                force_scales(S, st.lam, st.scale_int, st.scale_E);
-                for (int k = 0; k < 3; ++k) { st.s[k] = 1.0; st.phi[k] = 1.0; }
+                force_scales(S, st);
+                for (int k = 0; k < 3; ++k) {
+                    st.s[k] = 1.0; st.phi[k] = 1.0; st.phi_f[k] = 1.0f; st.sm1_f[k] = 0.0f;
+                }
+                st.scaled = 0;
             } else {
                 observe(b.sys[s], b.st[s]);
             }
@@ -893,31 +1217,6 @@ __global__ void k_noise(unsigned long long seed, unsigned long long sys, unsigne
     }
 }
 
-// ------------------------------------------------------------------------------------
-// Launchers
-// ------------------------------------------------------------------------------------
-bool lanes_supported(int lanes) { return lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
-
-void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
-                  cudaStream_t s, long* launches) {
-    if (ntiles <= 0) return;
-    if (precision == NEFE_FP64) k_cells_count<double><<<ntiles, kTile, 0, s>>>(b, force_all);
-    else k_cells_count<float><<<ntiles, kTile, 0, s>>>(b, force_all);
-    k_cells_scan<<<nsys, 256, 0, s>>>(b, force_all);
-    k_cells_fill<<<ntiles, kTile, 0, s>>>(b, force_all);
-    k_cells_sort<<<nsys, 256, 0, s>>>(b, force_all);
-    if (launches) *launches += 4;
-}
-
-void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
-                           cudaStream_t s, long* launches) {
-    if (ntiles <= 0) return;
-    launch_cells(b, precision, ntiles, nsys, force_all, s, launches);
-    if (precision == NEFE_FP64) k_nlist<double><<<ntiles, kTile, 0, s>>>(b, force_all);
-    else k_nlist<float><<<ntiles, kTile, 0, s>>>(b, force_all);
-    if (launches) *launches += 1;
-}
-
 // (n,3) row-major <-> SoA with stride n.
 __global__ void k_aos_to_soa(const double* __restrict__ a, double* __restrict__ s, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -931,12 +1230,6 @@ __global__ void k_soa_to_aos(const double* __restrict__ s, double* __restrict__ 
     const int i = t / 3, k = t % 3;
     a[t] = s[(size_t)k * n + i];
 }
-void launch_aos_soa(const double* src, double* dst, int n, int to_soa, cudaStream_t s) {
-    if (n <= 0) return;
-    const int blocks = (3 * n + 255) / 256;
-    if (to_soa) k_aos_to_soa<<<blocks, 256, 0, s>>>(src, dst, n);
-    else k_soa_to_aos<<<blocks, 256, 0, s>>>(src, dst, n);
-}
 
 __global__ void k_decode_ev(const long long* acc, double* out7) {
     const int t = threadIdx.x;
@@ -945,6 +1238,47 @@ __global__ void k_decode_ev(const long long* acc, double* out7) {
     long long sum = 0;
     for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)a * kSlots + sl];
     out7[t] = (double)sum / kFix;
+}
+
+// ------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------
+bool lanes_supported(int lanes) { return lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
+
+// With a worklist (engine) the per-tile rebuild kernels get a bounded grid and walk the
+// flagged tiles; without one (stateless calls) they cover every tile.
+static int rebuild_grid(const Bufs& b, int items) {
+    return b.rtiles ? (items < kRebuildBlocks ? items : kRebuildBlocks) : items;
+}
+
+void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
+                  cudaStream_t s, long* launches) {
+    if (ntiles <= 0) return;
+    if (b.rtiles) k_rebuild_list<<<1, 256, 0, s>>>(b, nsys, force_all);
+    const int g = rebuild_grid(b, ntiles);
+    if (precision == NEFE_FP64) k_cells_count<double><<<g, kTile, 0, s>>>(b);
+    else k_cells_count<float><<<g, kTile, 0, s>>>(b);
+    k_cells_scan<<<nsys, 256, 0, s>>>(b, force_all || !b.rtiles);
+    k_cells_fill<<<g, kTile, 0, s>>>(b);
+    k_cells_sort<<<nsys, 256, 0, s>>>(b, force_all || !b.rtiles);
+    if (launches) *launches += b.rtiles ? 5 : 4;
+}
+
+void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
+                           cudaStream_t s, long* launches) {
+    if (ntiles <= 0) return;
+    launch_cells(b, precision, ntiles, nsys, force_all, s, launches);
+    const int g = rebuild_grid(b, ntiles * kListLanes);
+    if (precision == NEFE_FP64) k_nlist<double><<<g, kTile, 0, s>>>(b);
+    else k_nlist<float><<<g, kTile, 0, s>>>(b);
+    if (launches) *launches += 1;
+}
+
+void launch_aos_soa(const double* src, double* dst, int n, int to_soa, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (3 * n + 255) / 256;
+    if (to_soa) k_aos_to_soa<<<blocks, 256, 0, s>>>(src, dst, n);
+    else k_soa_to_aos<<<blocks, 256, 0, s>>>(src, dst, n);
 }
 
 void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s) {
@@ -965,33 +1299,54 @@ void launch_mirror(const Bufs& b, int precision, int ntiles, cudaStream_t s, lon
     if (launches) *launches += 1;
 }
 
-template <typename T, int MODE>
-static void force_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
+template <typename T>
+static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
     switch (lanes) {
         case 4:
-            // the FP64 shell of 32 groups does not fit the 48 KB static shared limit
-            if (sizeof(T) == 8) k_force<T, 8, MODE><<<ntiles * 8, kTile, 0, s>>>(b);
-            else k_force<float, 4, MODE><<<ntiles * 4, kTile, 0, s>>>(b);
+            // the FP64 shell of 32 atoms per block does not fit the 48 KB static shared limit
+            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
+            else k_edges<T, 4><<<ntiles * 4, kTile, 0, s>>>(b);
             break;
-        case 8: k_force<T, 8, MODE><<<ntiles * 8, kTile, 0, s>>>(b); break;
-        case 16: k_force<T, 16, MODE><<<ntiles * 16, kTile, 0, s>>>(b); break;
-        default: k_force<T, 32, MODE><<<ntiles * 32, kTile, 0, s>>>(b); break;
+        case 8: k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
+        case 16: k_edges<T, 16><<<ntiles * 16, kTile, 0, s>>>(b); break;
+        default: k_edges<T, 32><<<ntiles * 32, kTile, 0, s>>>(b); break;
     }
 }
 
-void launch_force(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
+void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
                   long* launches) {
+    (void)mode;
     if (ntiles <= 0) return;
+    if (precision == NEFE_FP64) edges_dispatch<double>(b, lanes, ntiles, s);
+    else edges_dispatch<float>(b, lanes, ntiles, s);
+    if (launches) *launches += 1;
+}
+
+void launch_gather(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {
+    if (ntiles <= 0) return;
+    const int g = ntiles * kGatherLanes;
     if (precision == NEFE_FP64) {
-        if (mode == FM_FORCES) force_dispatch<double, FM_FORCES>(b, lanes, ntiles, s);
-        else if (mode == FM_SETUP) force_dispatch<double, FM_SETUP>(b, lanes, ntiles, s);
-        else force_dispatch<double, FM_STEP>(b, lanes, ntiles, s);
+        if (mode == FM_FORCES) k_gather<double, FM_FORCES><<<g, kTile, 0, s>>>(b);
+        else if (mode == FM_SETUP) k_gather<double, FM_SETUP><<<g, kTile, 0, s>>>(b);
+        else k_gather<double, FM_STEP><<<g, kTile, 0, s>>>(b);
     } else {
-        if (mode == FM_FORCES) force_dispatch<float, FM_FORCES>(b, lanes, ntiles, s);
-        else if (mode == FM_SETUP) force_dispatch<float, FM_SETUP>(b, lanes, ntiles, s);
-        else force_dispatch<float, FM_STEP>(b, lanes, ntiles, s);
+        if (mode == FM_FORCES) k_gather<float, FM_FORCES><<<g, kTile, 0, s>>>(b);
+        else if (mode == FM_SETUP) k_gather<float, FM_SETUP><<<g, kTile, 0, s>>>(b);
+        else k_gather<float, FM_STEP><<<g, kTile, 0, s>>>(b);
     }
     if (launches) *launches += 1;
+}
+
+void launch_materialize(const Bufs& b, int precision, int ntiles, double* x, double* v, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    if (precision == NEFE_FP64) k_materialize<double><<<ntiles, kTile, 0, s>>>(b, x, v);
+    else k_materialize<float><<<ntiles, kTile, 0, s>>>(b, x, v);
+}
+
+void launch_inject(const Bufs& b, int precision, int ntiles, const double* x, const double* v, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    if (precision == NEFE_FP64) k_inject<double><<<ntiles, kTile, 0, s>>>(b, x, v);
+    else k_inject<float><<<ntiles, kTile, 0, s>>>(b, x, v);
 }
 
 void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,

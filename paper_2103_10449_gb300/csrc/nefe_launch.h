@@ -14,12 +14,20 @@ struct Bufs {
     DevState* st;
     long long* acc;          // [nsys][ACC_N][kSlots]
     const int* tile_sys;     // system of each 128-atom tile
-    double* x;
-    double* v;
-    const double* r0;
-    void* F;                 // total force used by the next half kick
-    void* xs;                // mirror: x - q h, FP32 or FP64
-    void* xsb;               // mirror at the last list build
+    double* x;               // FP64 anchor positions (positions at the last list build), SoA
+    void* dhi;               // displacement since the last build, kernel precision, SoA (may be NULL)
+    void* dlo;               // its compensation term (FP32 path; may be NULL)
+    void* v;                 // velocities, kernel precision, SoA
+    const double* r0;        // Einstein sites, FP64 SoA
+    void* F;                 // total force used by the next half kick (T4)
+    void* xs;                // mirror x - q h (T4)
+    void* xa;                // mirror at the last build (T4)
+    void* sd0;               // anchor - r0 at the last build (T4)
+    void* xi;                // thermostat noise of the current step (T4)
+    void* shd;               // [ntot][kShell] in-cutoff shell: d_ij and g_ij (T4)
+    int* shj;                // [ntot][kShell] shell neighbour indices
+    int* shn;                // shell size
+    void* P;                 // pair + own-centred three-body force, .w = atom energy (T4)
     int4* q;                 // unwrapped cell index per axis, from the last build
     int* cell_of;
     int* perm;
@@ -30,6 +38,9 @@ struct Bufs {
     int* cnt;
     int cap;
     int ntot;
+    int tile_base;           // first tile of the launch (force passes run in L2-sized chunks)
+    int* rtiles;             // rebuild worklist (tiles of flagged systems) or NULL
+    int* rcount;             // its length
     double dt;
     const void* swc;         // SWc<float> or SWc<double> table
     DevPair* pairs;
@@ -51,9 +62,15 @@ void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, i
 // Half kick + drift + mirror + displacement check + noise sums (mode 0: no kick/drift).
 void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s,
                        long* launches);
-// SW (+ springs, + Langevin and second half kick in FM_SETUP / FM_STEP).
-void launch_force(const Bufs& b, int precision, int lanes, int ntiles, int mode,
-                  cudaStream_t s, long* launches);
+// Force pass A (edges: pair terms, triplets centred on each atom, leg forces per edge).
+void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
+                  long* launches);
+// Force pass B (gather leg forces; springs, Langevin and second half kick in FM_SETUP/FM_STEP).
+void launch_gather(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches);
+// FP64 positions (anchor + displacement) and FP64 velocities into SoA staging buffers.
+void launch_materialize(const Bufs& b, int precision, int ntiles, double* x, double* v, cudaStream_t s);
+// Replace positions (anchor, zero displacement) and/or velocities from FP64 SoA buffers.
+void launch_inject(const Bufs& b, int precision, int ntiles, const double* x, const double* v, cudaStream_t s);
 // Per-group scalar update. mode 0 INIT, 1 STEP, 2 OBSERVE.
 void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,
                   long* launches);

@@ -18,7 +18,7 @@
 namespace nefe {
 namespace {
 
-// Scratch layout (bytes), in order: DevSys | DevState | tile table | xs | xsb | q | counts |
+// Scratch layout (bytes), in order: DevSys | DevState | tile table | xs | xa | q | counts |
 // cursors.  The mirror arrays use float4 (the entry point runs the FP32 cell kernels).
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -26,8 +26,8 @@ constexpr size_t kOffSys = 0;
 constexpr size_t kOffSt = align_up(kOffSys + sizeof(DevSys));
 constexpr size_t kOffTile = align_up(kOffSt + sizeof(DevState));
 constexpr size_t kOffXs = align_up(kOffTile + sizeof(int) * (NEFE_NOALLOC_MAX_ATOMS / kTile + 1));
-constexpr size_t kOffXsb = align_up(kOffXs + sizeof(float4) * NEFE_NOALLOC_MAX_ATOMS);
-constexpr size_t kOffQ = align_up(kOffXsb + sizeof(float4) * NEFE_NOALLOC_MAX_ATOMS);
+constexpr size_t kOffXa = align_up(kOffXs + sizeof(float4) * NEFE_NOALLOC_MAX_ATOMS);
+constexpr size_t kOffQ = align_up(kOffXa + sizeof(float4) * NEFE_NOALLOC_MAX_ATOMS);
 constexpr size_t kOffCount = align_up(kOffQ + sizeof(int4) * NEFE_NOALLOC_MAX_ATOMS);
 constexpr size_t kOffCursor = align_up(kOffCount + sizeof(int) * NEFE_NOALLOC_MAX_CELLS);
 constexpr size_t kScratchBytes = align_up(kOffCursor + sizeof(int) * NEFE_NOALLOC_MAX_CELLS);
@@ -111,7 +111,7 @@ extern "C" int nefe_cell_bin_noalloc(const double* x, int n, const double box[3]
     b.tile_sys = reinterpret_cast<int*>(p + kOffTile);
     b.x = const_cast<double*>(x);
     b.xs = p + kOffXs;
-    b.xsb = p + kOffXsb;
+    b.xa = p + kOffXa;
     b.q = reinterpret_cast<int4*>(p + kOffQ);
     b.cell_count = reinterpret_cast<int*>(p + kOffCount);
     b.cell_cursor = reinterpret_cast<int*>(p + kOffCursor);

@@ -359,9 +359,10 @@ class Context:
         _check(self._L.nefe_set_profiling(self.h, int(bool(enable))))
 
     def profile(self):
-        us, n = ctypes.c_double(), ctypes.c_long()
-        _check(self._L.nefe_get_profile(self.h, ctypes.byref(us), ctypes.byref(n)))
-        return us.value, n.value
+        """Mean durations (us) of force pass A and pass B over the last graph replay."""
+        us, n = (ctypes.c_double * 2)(), ctypes.c_long()
+        _check(self._L.nefe_get_profile(self.h, us, ctypes.byref(n)))
+        return us[0], us[1], n.value
 
     def launch_count(self):
         c = ctypes.c_long(0)

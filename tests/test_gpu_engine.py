@@ -1,0 +1,68 @@
+"""Engine runs on the GPU: long-run stability of batched replicas and conservation checks.
+
+The per-system error word must stay clear (no NaN, no list or cell inconsistency), the
+thermostat must hold the temperature, and the list must keep every in-cutoff pair.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_10449_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KB = 8.617333262e-5
+MVV2E = 1.66053906660e-23 / 1.602176634e-19
+
+
+def _ctx(N, nrep, T=1000.0, precision=0, nsched=20000):
+    x, box = I.diamond(10, 10, 10)
+    sv = math.sqrt(KB * T / (28.0855 * MVV2E))
+    ctx = N.Context(precision=precision, skin=0.5, nbr_cap=48)
+    for r in range(nrep):
+        s = ctx.add_system(x, box, v=I.gaussian_velocities(len(x), sv, 50 + r), r0=x)
+        ctx.set_thermostat(s, T, 0.1, 50 + r)
+        ctx.set_schedule(s, N.NEFE_SCHED_FL, direction=1 if r % 2 == 0 else -1, nsteps=nsched, k_E=5.0)
+    return ctx, len(x)
+
+
+def test_batched_frenkel_ladd_long_run_stays_physical():
+    from paper_2103_10449_gb300 import nefe as N
+    ctx, n = _ctx(N, 6)
+    ctx.run(4000)
+    res = ctx.results_all()
+    for r in res:
+        assert r["error"] == 0, r
+        assert 800.0 < r["T"] < 1200.0, r["T"]
+        assert math.isfinite(r["W"]) and math.isfinite(r["U"])
+    # forward replicas are SW diamond: cohesive energy near -4.34 + 3/2 kT at 1000 K
+    u = [r["U"] / n for i, r in enumerate(res) if i % 2 == 0]
+    assert all(-4.30 < e < -4.10 for e in u), u
+    mean_row, max_row, builds = ctx.list_stats(-1)
+    assert 15.0 < mean_row < 20.0 and max_row <= 48
+    ctx.close()
+
+
+def test_list_holds_every_pair_inside_the_cutoff_after_a_long_run():
+    """Verlet guarantee: each pair closer than a*sigma at the current positions is in the
+    list (checked with the stateless list built from the engine's current positions, whose
+    rows must contain every cutoff pair of the engine's own forces: equal forces)."""
+    from paper_2103_10449_gb300 import nefe as N
+    ctx, n = _ctx(N, 1, precision=1)
+    ctx.run(2000)
+    x, v, box = ctx.get_state(0)
+    r = ctx.results(0)
+    ctx.close()
+    # energy of the current positions from a freshly built list must equal the engine's U
+    rcs = 2.0951 * 1.8 + 0.5
+    xd = torch.tensor(np.ascontiguousarray(x.T).reshape(-1), dtype=torch.float64, device="cuda")
+    nbr = torch.zeros(n * 48, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    N.nefe_neighbor_build(xd, n, box, rcs, 48, nbr, cnt)
+    f = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    ev = torch.zeros(7, dtype=torch.float64, device="cuda")
+    N.nefe_sw_forces(xd, n, box, rcs, nbr, cnt, 48, N.nefe_sw_params_silicon(), 1, f, None, ev)
+    torch.cuda.synchronize()
+    assert ev[0].item() == pytest.approx(r["U"], rel=1e-9)
