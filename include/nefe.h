@@ -311,11 +311,15 @@ NEFE_API int nefe_get_trace(nefe_ctx* ctx, int sys, double* buf, long cap, long*
 NEFE_API int nefe_save(nefe_ctx* ctx, const char* path);
 NEFE_API int nefe_load(nefe_ctx* ctx, const char* path);
 
-/* Times each supported lanes-per-atom variant of the force kernel on the current state and
- * keeps the fastest (result readable with nefe_get_tuning). */
+/* Times the variants of both force passes on the current state and keeps the fastest:
+ * pass A with 1 (one thread per atom), 4, 8, 16 or 32 lanes per atom (FP64: 8, 16, 32),
+ * pass B with 1 or 4 lanes per atom.  nefe_get_tuning reports pass A's lanes and the summed
+ * time of the two chosen passes; nefe_set_tuning fixes pass A's lanes. */
 NEFE_API int nefe_autotune(nefe_ctx* ctx);
 NEFE_API int nefe_get_tuning(nefe_ctx* ctx, int* lanes_per_atom, double* best_us);
 NEFE_API int nefe_set_tuning(nefe_ctx* ctx, int lanes_per_atom);
+/* Fixes pass B's lanes per atom (1 or 4). */
+NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
 
 /* Batched state transfer for every system at once: host (Ntot, 3) arrays, systems in the
  * order they were added (Ntot = sum of their n).  One host<->device copy each, the layout

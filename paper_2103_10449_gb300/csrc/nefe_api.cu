@@ -90,6 +90,8 @@ static int prepare1(Scratch1& S, int n, const double box[3], double rcs, int nce
     std::memset(&hs, 0, sizeof(hs));
     hs.off = 0; hs.n = n; hs.tile0 = 0; hs.ntile = ntiles; hs.cell0 = 0; hs.ncell_cap = ncell_cap;
     hs.rcs = rcs; hs.pair = -1; hs.prm = 0; hs.mass_e = 1.0;
+    hs.rcs2_lo_f = (float)(rcs * rcs) * (1.0f - 1e-4f);
+    hs.rcs2_hi_f = (float)(rcs * rcs) * (1.0f + 1e-4f);
     DevState st;
     std::memset(&st, 0, sizeof(st));
     for (int k = 0; k < 3; ++k) st.box[k] = box[k];
@@ -241,7 +243,7 @@ int nefe_sw_forces(const double* x, int n, const double box[3], double rcs, cons
         const int ntiles = (n + kTile - 1) / kTile;
         launch_mirror(b, precision, ntiles, S.s, nullptr);
         launch_edges(b, precision, 8, ntiles, FM_FORCES, S.s, nullptr);
-        launch_gather(b, precision, ntiles, FM_FORCES, S.s, nullptr);
+        launch_gather(b, precision, 4, ntiles, FM_FORCES, S.s, nullptr);
         NEFE_CU(cudaGetLastError());
     }
     if (energy_virial) launch_decode_ev(S.acc, energy_virial, S.s);

@@ -43,6 +43,8 @@ struct SWc {
     T epslam;      // eps * lambda3
     T gam;
     T c0;
+    T s_act;       // edges with r/sigma >= s_act are dropped (see make_swc)
+    T act2;        // (s_act sigma)^2
     int int_pq;    // 1 when p == 4 and q == 0 (the standard set): s^-p by multiplications
 };
 
@@ -66,6 +68,7 @@ struct DevSys {
     double ckick;               // dt / (2 m) (A^2 / (eV ps))
     // FP32 copies and flags read by the FP32 kernels (no FP64 instruction per atom)
     float amp_f, gam_f, ckick_f, mass_f, kE_f, kint_f, dt_f, inv_n_f;
+    float rcs2_lo_f, rcs2_hi_f; // list radius^2 times (1 -/+ 1e-4): FP32 filter band
     int thermo;                 // tdamp > 0
     int springs;                // an Einstein spring acts (FL reference or U_int = Einstein)
     int trace_every;

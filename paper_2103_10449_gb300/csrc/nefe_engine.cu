@@ -19,7 +19,7 @@ namespace {
 constexpr int kGraphSteps = 32;
 // The two force passes run chunk by chunk (whole systems, at most this many atoms) so that
 // the shells pass A writes are still in L2 when pass B reads them.
-constexpr int kChunkAtoms = 1 << 18;
+constexpr int kChunkAtomsDefault = 1 << 18;
 // launches per step: group, kick-drift, 6 rebuild kernels, then 2 force passes per chunk
 int launches_per_step(const nefe_ctx* c);
 
@@ -79,7 +79,8 @@ struct nefe_ctx {
     DevGroup* d_groups = nullptr;
     double* d_trace = nullptr;
     std::vector<void*> allocs;
-    int lanes = 8;
+    int lanes = 8;           // pass A lanes per atom (1 = one thread per atom)
+    int glanes = 4;          // pass B lanes per atom
     double tune_us = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -87,12 +88,35 @@ struct nefe_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> ev0, ev1, ev2;   // around the force passes of the captured graph
     std::vector<int> chunk_tile0, chunk_ntile;
+    int chunk_atoms = 1 << 18;   // force passes run over whole systems of at most this many atoms
+    std::vector<int> sys_tile0, sys_n;
+    int ntiles_total = 0;
     Bufs b{};
 };
 
 namespace {
 
 int launches_per_step(const nefe_ctx* c) { return 8 + 2 * (int)c->chunk_tile0.size(); }
+
+// Groups whole systems into chunks of at most `atoms` atoms (a larger system is a chunk of
+// its own).
+void plan_chunks(nefe_ctx* c, int atoms_max) {
+    c->chunk_atoms = atoms_max;
+    c->chunk_tile0.clear();
+    c->chunk_ntile.clear();
+    int t0 = 0, atoms = 0;
+    for (size_t s = 0; s < c->sys_n.size(); ++s) {
+        if (atoms > 0 && (long long)atoms + c->sys_n[s] > atoms_max) {
+            c->chunk_tile0.push_back(t0);
+            c->chunk_ntile.push_back(c->sys_tile0[s] - t0);
+            t0 = c->sys_tile0[s];
+            atoms = 0;
+        }
+        atoms += c->sys_n[s];
+    }
+    c->chunk_tile0.push_back(t0);
+    c->chunk_ntile.push_back(c->ntiles_total - t0);
+}
 
 int set_device(nefe_ctx* c) {
     NEFE_CU(cudaSetDevice(c->device));
@@ -134,7 +158,7 @@ void enqueue_forces(nefe_ctx* c, int mode, int slot = -1) {
         if (prof) cudaEventRecordWithFlags(c->ev0[e], c->stream, cudaEventRecordExternal);
         launch_edges(b, c->prec, c->lanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
         if (prof) cudaEventRecordWithFlags(c->ev1[e], c->stream, cudaEventRecordExternal);
-        launch_gather(b, c->prec, c->chunk_ntile[k], mode, c->stream, &c->launches);
+        launch_gather(b, c->prec, c->glanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
         if (prof) cudaEventRecordWithFlags(c->ev2[e], c->stream, cudaEventRecordExternal);
     }
 }
@@ -181,6 +205,24 @@ int resetup(nefe_ctx* c) {
     launch_kick_drift(c->b, c->prec, c->ntiles, 0, c->stream, &c->launches);
     enqueue_forces(c, FM_SETUP);
     NEFE_CU(cudaGetLastError());
+    return NEFE_OK;
+}
+
+// Event slots for profiling: three per chunk per captured step.
+int ensure_events(nefe_ctx* c) {
+    const size_t ne = (size_t)kGraphSteps * std::max<size_t>(1, c->chunk_tile0.size());
+    if (c->ev0.size() == ne) return NEFE_OK;
+    for (auto e : c->ev0) cudaEventDestroy(e);
+    for (auto e : c->ev1) cudaEventDestroy(e);
+    for (auto e : c->ev2) cudaEventDestroy(e);
+    c->ev0.assign(ne, nullptr);
+    c->ev1.assign(ne, nullptr);
+    c->ev2.assign(ne, nullptr);
+    for (size_t k = 0; k < ne; ++k) {
+        NEFE_CU(cudaEventCreate(&c->ev0[k]));
+        NEFE_CU(cudaEventCreate(&c->ev1[k]));
+        NEFE_CU(cudaEventCreate(&c->ev2[k]));
+    }
     return NEFE_OK;
 }
 
@@ -248,6 +290,8 @@ int setup(nefe_ctx* c) {
         d.mass_f = (float)d.mass_e; d.kE_f = (float)d.k_E; d.kint_f = (float)d.k_int;
         d.dt_f = (float)c->dt;
         d.inv_n_f = (float)(1.0 / h.n);
+        d.rcs2_lo_f = (float)(rcs * rcs) * (1.0f - 1e-4f);
+        d.rcs2_hi_f = (float)(rcs * rcs) * (1.0f + 1e-4f);
         d.thermo = h.tdamp > 0.0 ? 1 : 0;
         d.springs = (d.k_E > 0.0 || h.pot == NEFE_POT_EINSTEIN) ? 1 : 0;
         d.trace_every = h.trace_every;
@@ -264,22 +308,11 @@ int setup(nefe_ctx* c) {
         tr += h.trace_every > 0 ? h.trace_cap : 0;
     }
     if (ntot >= (1LL << kCodeShift)) return fail(NEFE_EINVAL, "more than 2^27 atoms in one context");
-    c->chunk_tile0.clear();
-    c->chunk_ntile.clear();
-    {
-        int t0 = 0, atoms = 0;
-        for (int s = 0; s < nsys; ++s) {
-            if (atoms > 0 && atoms + hs[s].n > kChunkAtoms) {
-                c->chunk_tile0.push_back(t0);
-                c->chunk_ntile.push_back(hs[s].tile0 - t0);
-                t0 = hs[s].tile0;
-                atoms = 0;
-            }
-            atoms += hs[s].n;
-        }
-        c->chunk_tile0.push_back(t0);
-        c->chunk_ntile.push_back((int)tile_sys.size() - t0);
-    }
+    c->sys_tile0.resize(nsys);
+    c->sys_n.resize(nsys);
+    for (int s = 0; s < nsys; ++s) { c->sys_tile0[s] = hs[s].tile0; c->sys_n[s] = hs[s].n; }
+    c->ntiles_total = (int)tile_sys.size();
+    plan_chunks(c, c->chunk_atoms);
     c->ntot = (int)ntot;
     c->ntiles = (int)tile_sys.size();
     c->nsys = nsys;
@@ -586,6 +619,7 @@ int nefe_run(nefe_ctx* c, long nsteps) {
     if ((rc = set_device(c))) return rc;
     long full = nsteps / kGraphSteps, rem = nsteps % kGraphSteps;
     if (full > 0 && !c->gexec) {
+        if (c->profiling && (rc = ensure_events(c))) return rc;
         NEFE_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         long before = c->launches;
         for (int k = 0; k < kGraphSteps; ++k) enqueue_step(c, c->profiling ? k : -1);
@@ -823,28 +857,55 @@ int nefe_autotune(nefe_ctx* c) {
     cudaEvent_t e0, e1;
     NEFE_CU(cudaEventCreate(&e0));
     NEFE_CU(cudaEventCreate(&e1));
-    const int cand[4] = {4, 8, 16, 32};
+    auto time_us = [&](auto&& launch) {
+        for (int w = 0; w < 2; ++w) launch();
+        cudaEventRecord(e0, c->stream);
+        const int reps = 5;
+        for (int r = 0; r < reps; ++r) launch();
+        cudaEventRecord(e1, c->stream);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        return 1000.0 * ms / reps;
+    };
+    const int cand[5] = {1, 4, 8, 16, 32};
     double best = 1e30;
     int best_l = c->lanes;
     for (int l : cand) {
-        if (c->prec == NEFE_FP64 && l == 4) continue;
-        for (int w = 0; w < 2; ++w) launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches);
-        cudaEventRecord(e0, c->stream);
-        const int reps = 5;
-        for (int r = 0; r < reps; ++r) launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches);
-        cudaEventRecord(e1, c->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double us = 1000.0 * ms / reps;
+        if (c->prec == NEFE_FP64 && (l == 1 || l == 4)) continue;
+        const double us = time_us([&] { launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches); });
         if (us < best) { best = us; best_l = l; }
     }
+    launch_edges(b, c->prec, best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
+    double best_g = 1e30;
+    int best_gl = c->glanes;
+    for (int l : {1, 4}) {
+        const double us = time_us([&] { launch_gather(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches); });
+        if (us < best_g) { best_g = us; best_gl = l; }
+    }
+    // chunking of the two passes (L2 residency of the shells against parallelism per launch)
+    const int old_chunk = c->chunk_atoms;
+    double best_c = 1e30;
+    int best_ca = old_chunk;
+    for (int ca : {1 << 17, 1 << 18, 1 << 19, 1 << 30}) {
+        plan_chunks(c, ca);
+        const double us = time_us([&] {
+            for (size_t k = 0; k < c->chunk_tile0.size(); ++k) {
+                Bufs bk = b;
+                bk.tile_base = c->chunk_tile0[k];
+                launch_edges(bk, c->prec, best_l, c->chunk_ntile[k], FM_FORCES, c->stream, &c->launches);
+                launch_gather(bk, c->prec, best_gl, c->chunk_ntile[k], FM_FORCES, c->stream, &c->launches);
+            }
+        });
+        if (us < best_c) { best_c = us; best_ca = ca; }
+    }
+    plan_chunks(c, best_ca);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     NEFE_CU(cudaGetLastError());
-    if (best_l != c->lanes) drop_graph(c);
+    if (best_l != c->lanes || best_gl != c->glanes || best_ca != old_chunk) drop_graph(c);
     c->lanes = best_l;
-    c->tune_us = best;
+    c->glanes = best_gl;
+    c->tune_us = best_c;
     return NEFE_OK;
 }
 
@@ -857,7 +918,7 @@ int nefe_get_tuning(nefe_ctx* c, int* lanes, double* best_us) {
 
 int nefe_set_tuning(nefe_ctx* c, int lanes) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
-    if (!lanes_supported(lanes) || (c->prec == NEFE_FP64 && lanes == 4))
+    if (!lanes_supported(lanes) || (c->prec == NEFE_FP64 && (lanes == 1 || lanes == 4)))
         return fail(NEFE_EINVAL, "unsupported lanes per atom %d", lanes);
     if (lanes != c->lanes) drop_graph(c);
     c->lanes = lanes;
@@ -959,23 +1020,12 @@ int nefe_set_profiling(nefe_ctx* c, int enable) {
     if ((bool)enable == c->profiling) return NEFE_OK;
     drop_graph(c);
     c->profiling = enable != 0;
-    if (c->profiling && c->ev0.empty()) {
-        const int ne = kGraphSteps * std::max<int>(1, (int)c->chunk_tile0.size());
-        c->ev0.resize(ne);
-        c->ev1.resize(ne);
-        c->ev2.resize(ne);
-        for (int k = 0; k < ne; ++k) {
-            NEFE_CU(cudaEventCreate(&c->ev0[k]));
-            NEFE_CU(cudaEventCreate(&c->ev1[k]));
-            NEFE_CU(cudaEventCreate(&c->ev2[k]));
-        }
-    }
     return NEFE_OK;
 }
 
 int nefe_get_profile(nefe_ctx* c, double* us, long* samples) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
-    if (!c->profiling || c->ev0.empty()) return fail(NEFE_ESTATE, "profiling is not enabled");
+    if (!c->profiling || c->ev0.empty()) return fail(NEFE_ESTATE, "profiling is not enabled or no graph ran yet");
     int rc = set_device(c);
     if (rc) return rc;
     NEFE_CU(cudaStreamSynchronize(c->stream));
@@ -1006,6 +1056,14 @@ int nefe_get_profile(nefe_ctx* c, double* us, long* samples) {
         us[1] = n > 0 ? 1000.0 * tb / n : 0.0;
     }
     if (samples) *samples = n;
+    return NEFE_OK;
+}
+
+int nefe_set_gather_tuning(nefe_ctx* c, int lanes) {
+    if (!c) return fail(NEFE_EINVAL, "context is NULL");
+    if (lanes != 1 && lanes != 4) return fail(NEFE_EINVAL, "pass B supports 1 or 4 lanes per atom");
+    if (lanes != c->glanes) drop_graph(c);
+    c->glanes = lanes;
     return NEFE_OK;
 }
 

@@ -46,6 +46,14 @@ inline SWc<T> make_swc(const nefe_sw_params& p) {
     c.epslam = (T)(p.eps * p.lambda3);
     c.gam = (T)p.gamma;
     c.c0 = (T)p.cos0;
+    // FP32 path: an edge whose three-body factor exp(gamma/(s - a)) is below 1e-12 adds forces
+    // of order 1e-8 eV/A (pair and triplet), far below FP32 resolution, so it is dropped:
+    // s_act = a + gamma / ln(1e-12).  FP64 path: only the last 1e-12 sigma before the cutoff
+    // (where the terms underflow to 0) is dropped.
+    if (sizeof(T) == 4) c.s_act = (T)(p.a + p.gamma / std::log(1e-12));
+    else c.s_act = (T)(p.a - 1e-12);
+    const double ract = (double)c.s_act * p.sigma;
+    c.act2 = (T)(ract * ract < rc * rc ? ract * ract : rc * rc);
     c.int_pq = (p.p == 4.0 && p.q == 0.0) ? 1 : 0;
     return c;
 }

@@ -127,8 +127,8 @@ __device__ __forceinline__ void block_sum_to_acc(T (&v)[K], long long* acc_sys, 
     __syncthreads();
     if (threadIdx.x < K) {
         T s = 0;
-#pragma unroll
-        for (int i = 0; i < kTile / 32; ++i) s += red[i][threadIdx.x];
+        const int nw = (int)(blockDim.x >> 5);
+        for (int i = 0; i < nw; ++i) s += red[i][threadIdx.x];
         long long q;
         bool bad;
         if constexpr (sizeof(T) == 4) {
@@ -427,26 +427,34 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     const int cell = b.cell_of[i];
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
     const int* start = b.cell_start + S.cell0 + ta.sys;
-    // per-group table of the 27 cells and the prefix of their occupancy
+    // per-group table of the 27 cells (lanes share the work) and the prefix of their occupancy
+    for (int o = lane; o < 27; o += L) {
+        int xx = cx + o % 3 - 1, yy = cy + (o / 3) % 3 - 1, zz = cz + o / 9 - 1;
+        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        const int c2 = xx + nx * (yy + ny * zz);
+        const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
+        ccell[grp][o] = c2;
+        cstart[grp][o + 1] = hi - lo;
+    }
+    __syncwarp(gmask);
     if (lane == 0) {
-        int acc = 0;
-        for (int o = 0; o < 27; ++o) {
-            const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-            const int c2 = (cx + ox + nx) % nx + nx * (((cy + oy + ny) % ny) + ny * ((cz + oz + nz) % nz));
-            ccell[grp][o] = c2;
-            cstart[grp][o] = acc;
-            const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
-            acc += hi - lo;
-        }
-        cstart[grp][27] = acc;
+        cstart[grp][0] = 0;
+        for (int o = 1; o <= 27; ++o) cstart[grp][o] += cstart[grp][o - 1];
     }
     __syncwarp(gmask);
     const int total = cstart[grp][27];
     const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
-    const T hx = (T)st.h[0], hy = (T)st.h[1], hz = (T)st.h[2];
-    const double rcs2 = __dmul_rn(S.rcs, S.rcs);
-    const T band = sizeof(T) == 4 ? (T)1e-4 : (T)1e-10;
-    const T lo2 = (T)rcs2 * ((T)1 - band), hi2 = (T)rcs2 * ((T)1 + band);
+    const T hx = pick<T>(st.h[0], st.h_f[0]), hy = pick<T>(st.h[1], st.h_f[1]), hz = pick<T>(st.h[2], st.h_f[2]);
+    T lo2, hi2;
+    if constexpr (sizeof(T) == 4) {
+        lo2 = S.rcs2_lo_f;
+        hi2 = S.rcs2_hi_f;
+    } else {
+        lo2 = S.rcs * S.rcs * (1.0 - 1e-10);
+        hi2 = S.rcs * S.rcs * (1.0 + 1e-10);
+    }
     const int cap = b.cap;
     int count = 0;
     int o = 0;
@@ -471,7 +479,7 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
                     in = true;
                 } else if (dd <= hi2) {
                     double d[3];
-                    in = exact_pair_in(b, st.box, i, j, rcs2, d);
+                    in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
                     in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
                          fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
                          fabs(d[2] - (double)dz) < 0.5 * st.h[2];
@@ -649,7 +657,7 @@ template <typename T> __device__ __forceinline__ T cut_eps() { return sizeof(T) 
 template <typename T>
 __device__ __forceinline__ void sw_edge(const SWc<T>& P, T r, T& phi, T& dphi, T& g, T& dg) {
     const T s = r * P.inv_sig;
-    if (!(s - P.a < -cut_eps<T>())) {
+    if (!(s < P.s_act) || !(s - P.a < -cut_eps<T>())) {
         phi = dphi = g = dg = (T)0;
         return;
     }
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
                 dy = (xj.y - xi.y) + oh.y;
                 dz = (xj.z - xi.z) + oh.z;
                 r2 = dx * dx + dy * dy + dz * dz;
-                in = r2 < P.rc2;
+                in = r2 < P.act2;
             }
             const unsigned bal = __ballot_sync(gmask, in);
             if (in) {
@@ -806,16 +814,129 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     block_sum_to_acc<T, 8>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
 
+// Force pass A, one thread per atom (64-thread blocks, half a tile each).  The row is first
+// compacted into the thread's active shell (kShell1 entries in shared memory, one column
+// per thread), then edges (pair terms, g, dg) and the triplets centred on the atom are
+// evaluated by the same thread, so no lane idles while another holds an edge.
+constexpr int kShell1 = 20;
+constexpr int kEdges1Threads = 64;
+template <typename T>
+__global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
+    using T4 = typename V4<T>::t;
+    constexpr int NT = kEdges1Threads;
+    __shared__ T4 sh_d[kShell1][NT];
+    __shared__ T sh_g[kShell1][NT];
+    __shared__ T sh_dg[kShell1][NT];
+    const int tile = blockIdx.x / (kTile / NT) + b.tile_base, part = blockIdx.x % (kTile / NT);
+    const TileAtom ta = tile_of(b, tile);
+    const DevSys& S = b.sys[ta.sys];
+    DevState& st = b.st[ta.sys];
+    if (S.pot != POT_SW) return;                 // uniform over the block
+    const SWc<T> P = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
+    __shared__ T4 soff[27];
+    offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
+    const int t = threadIdx.x;
+    const int ia = part * NT + t;
+    T fx = 0, fy = 0, fz = 0, en = 0;
+    T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    if (ia < ta.count) {
+        const int i = ta.first + ia;
+        const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
+        const int ci = min(b.cnt[i], b.cap);
+        const int* row = b.nbr + (size_t)i * b.cap;
+        T4* Sd = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
+        int* Sj = b.shj + (size_t)i * kShell;
+        int m = 0;
+        for (int base = 0; base < ci; base += 4) {       // compaction: distance test only,
+            int e[4];                                     // four candidates in flight (entries
+            T4 xj[4];                                     // with code >= 16 are negative ints)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = (base + u < ci) ? row[base + u] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (base + u < ci) xj[u] = reinterpret_cast<const T4*>(b.xs)[e[u] & (int)kIndexMask];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (base + u >= ci) continue;
+                const T4 oh = soff[(unsigned)e[u] >> kCodeShift];
+                const T dx = (xj[u].x - xi.x) + oh.x, dy = (xj[u].y - xi.y) + oh.y, dz = (xj[u].z - xi.z) + oh.z;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < P.act2) {
+                    if (m < kShell1) {
+                        sh_d[m][t] = mk4(dx, dy, dz, r2);
+                        Sj[m] = e[u] & (int)kIndexMask;
+                    }
+                    ++m;
+                }
+            }
+        }
+        if (m > kShell1) {
+            atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
+            m = kShell1;
+        }
+        for (int a = 0; a < m; ++a) {                    // edges: pair terms, g, dg
+            const T4 d = sh_d[a][t];
+            const T r = d.w * xrsqrt(d.w);
+            T phi, dphi, g, dg;
+            sw_edge<T>(P, r, phi, dphi, g, dg);
+            sh_d[a][t] = mk4(d.x, d.y, d.z, r);
+            sh_g[a][t] = g;
+            sh_dg[a][t] = dg;
+            Sd[a] = mk4(d.x, d.y, d.z, g);
+            const T c = dphi * xrcp(r);
+            fx += c * d.x; fy += c * d.y; fz += c * d.z;
+            en += (T)0.5 * phi;
+            const T hc = (T)-0.5 * c;
+            w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
+            w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
+        }
+        for (int a = 0; a < m - 1; ++a) {                // triplets centred at i
+            const T4 da = sh_d[a][t];
+            const T ga = sh_g[a][t], dga = sh_dg[a][t];
+            const T ira = xrcp(da.w);
+            const T uax = da.x * ira, uay = da.y * ira, uaz = da.z * ira;
+            for (int bb = a + 1; bb < m; ++bb) {
+                const T4 db = sh_d[bb][t];
+                const T gb = sh_g[bb][t], dgb = sh_dg[bb][t];
+                const T irb = xrcp(db.w);
+                const T ubx = db.x * irb, uby = db.y * irb, ubz = db.z * irb;
+                const T c = uax * ubx + uay * uby + uaz * ubz;
+                const T dc = c - P.c0;
+                const T two = (T)2 * P.epslam * dc * ga * gb;
+                const T dc2 = P.epslam * dc * dc;
+                const T ta_ = two * ira, tb_ = two * irb;
+                const T fax = -(ta_ * (ubx - c * uax) + dc2 * dga * gb * uax);
+                const T fay = -(ta_ * (uby - c * uay) + dc2 * dga * gb * uay);
+                const T faz = -(ta_ * (ubz - c * uaz) + dc2 * dga * gb * uaz);
+                const T fbx = -(tb_ * (uax - c * ubx) + dc2 * ga * dgb * ubx);
+                const T fby = -(tb_ * (uay - c * uby) + dc2 * ga * dgb * uby);
+                const T fbz = -(tb_ * (uaz - c * ubz) + dc2 * ga * dgb * ubz);
+                fx -= fax + fbx; fy -= fay + fby; fz -= faz + fbz;
+                en += dc2 * ga * gb;
+                w0 += da.x * fax + db.x * fbx;
+                w1 += da.y * fay + db.y * fby;
+                w2 += da.z * faz + db.z * fbz;
+                w3 += (T)0.5 * (da.x * fay + da.y * fax + db.x * fby + db.y * fbx);
+                w4 += (T)0.5 * (da.x * faz + da.z * fax + db.x * fbz + db.z * fbx);
+                w5 += (T)0.5 * (da.y * faz + da.z * fay + db.y * fbz + db.z * fby);
+            }
+        }
+        reinterpret_cast<T4*>(b.P)[i] = mk4(fx, fy, fz, en);
+        b.shn[i] = m;
+    }
+    T red[8] = {en, (T)0, w0, w1, w2, w3, w4, w5};
+    block_sum_to_acc<T, 8>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+}
+
 // Force pass B, one thread per atom:
 //   F_SW(i) = P(i) + sum_{j in shell(i)} sum_{k in shell(j), k != i} -d h(j; i, k) / d x_i
 // from the stored shells (d_ji = -d_ij, g_ji = g_ij; d_jk, g_jk from j's shell).  Then, in
 // FM_SETUP / FM_STEP: Einstein springs, lambda mixing, Langevin force (this step's noise with
 // its per-system mean removed), second half kick and the kinetic sums.
-constexpr int kGatherLanes = 4;
-template <typename T, int MODE>
+template <typename T, int MODE, int L>
 __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     using T4 = typename V4<T>::t;
-    constexpr int L = kGatherLanes, G = kTile / L;
+    constexpr int G = kTile / L;
     const int tile = blockIdx.x / L + b.tile_base, part = blockIdx.x % L;
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
@@ -836,7 +957,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     __syncthreads();
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
-    const unsigned gmask = ((1u << L) - 1u) << lbase;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
     const int ia = part * G + grp;
     T red[14];
 #pragma unroll
@@ -863,6 +984,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 const int mj = b.shn[j];
                 const T4* Sdj = Sd + (size_t)j * kShell;
                 const int* Sjj = b.shj + (size_t)j * kShell;
+#pragma unroll 4
                 for (int t = 0; t < mj; ++t) {
                     const T4 djk = Sdj[t];
                     if (Sjj[t] == i) continue;
@@ -1243,7 +1365,7 @@ __global__ void k_decode_ev(const long long* acc, double* out7) {
 // ------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------
-bool lanes_supported(int lanes) { return lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
+bool lanes_supported(int lanes) { return lanes == 1 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
 
 // With a worklist (engine) the per-tile rebuild kernels get a bounded grid and walk the
 // flagged tiles; without one (stateless calls) they cover every tile.
@@ -1302,6 +1424,11 @@ void launch_mirror(const Bufs& b, int precision, int ntiles, cudaStream_t s, lon
 template <typename T>
 static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
     switch (lanes) {
+        case 1:
+            // the FP64 one-thread shells exceed the static shared limit: use 8 lanes instead
+            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
+            else k_edges1<T><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
+            break;
         case 4:
             // the FP64 shell of 32 atoms per block does not fit the 48 KB static shared limit
             if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
@@ -1322,17 +1449,23 @@ void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode,
     if (launches) *launches += 1;
 }
 
-void launch_gather(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {
+template <typename T, int MODE>
+static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
+    if (lanes == 1) k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b);
+    else k_gather<T, MODE, 4><<<ntiles * 4, kTile, 0, s>>>(b);
+}
+
+void launch_gather(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
+                   long* launches) {
     if (ntiles <= 0) return;
-    const int g = ntiles * kGatherLanes;
     if (precision == NEFE_FP64) {
-        if (mode == FM_FORCES) k_gather<double, FM_FORCES><<<g, kTile, 0, s>>>(b);
-        else if (mode == FM_SETUP) k_gather<double, FM_SETUP><<<g, kTile, 0, s>>>(b);
-        else k_gather<double, FM_STEP><<<g, kTile, 0, s>>>(b);
+        if (mode == FM_FORCES) gather_dispatch<double, FM_FORCES>(b, lanes, ntiles, s);
+        else if (mode == FM_SETUP) gather_dispatch<double, FM_SETUP>(b, lanes, ntiles, s);
+        else gather_dispatch<double, FM_STEP>(b, lanes, ntiles, s);
     } else {
-        if (mode == FM_FORCES) k_gather<float, FM_FORCES><<<g, kTile, 0, s>>>(b);
-        else if (mode == FM_SETUP) k_gather<float, FM_SETUP><<<g, kTile, 0, s>>>(b);
-        else k_gather<float, FM_STEP><<<g, kTile, 0, s>>>(b);
+        if (mode == FM_FORCES) gather_dispatch<float, FM_FORCES>(b, lanes, ntiles, s);
+        else if (mode == FM_SETUP) gather_dispatch<float, FM_SETUP>(b, lanes, ntiles, s);
+        else gather_dispatch<float, FM_STEP>(b, lanes, ntiles, s);
     }
     if (launches) *launches += 1;
 }

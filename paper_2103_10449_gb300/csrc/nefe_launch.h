@@ -66,7 +66,8 @@ void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaS
 void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
                   long* launches);
 // Force pass B (gather leg forces; springs, Langevin and second half kick in FM_SETUP/FM_STEP).
-void launch_gather(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches);
+void launch_gather(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
+                   long* launches);
 // FP64 positions (anchor + displacement) and FP64 velocities into SoA staging buffers.
 void launch_materialize(const Bufs& b, int precision, int ntiles, double* x, double* v, cudaStream_t s);
 // Replace positions (anchor, zero displacement) and/or velocities from FP64 SoA buffers.

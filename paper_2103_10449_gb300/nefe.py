@@ -105,6 +105,7 @@ SIGNATURES = {
     "nefe_autotune": [_vp],
     "nefe_get_tuning": [_vp, _c_int_p, _c_dbl_p],
     "nefe_set_tuning": [_vp, ctypes.c_int],
+    "nefe_set_gather_tuning": [_vp, ctypes.c_int],
     "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
     "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
     "nefe_get_state_all": [_vp, _c_dbl_p, _c_dbl_p],
@@ -334,8 +335,10 @@ class Context:
         _check(self._L.nefe_get_tuning(self.h, ctypes.byref(lanes), ctypes.byref(us)))
         return lanes.value, us.value
 
-    def set_tuning(self, lanes):
+    def set_tuning(self, lanes, gather_lanes=None):
         _check(self._L.nefe_set_tuning(self.h, int(lanes)))
+        if gather_lanes is not None:
+            _check(self._L.nefe_set_gather_tuning(self.h, int(gather_lanes)))
 
     def set_state_all(self, x=None, v=None):
         """x, v: host (Ntot, 3) float64 arrays (pinned memory makes the copy faster)."""

@@ -173,7 +173,7 @@ def _sv(T):
     return math.sqrt(O.KB * T / (O.M_SI * O.MVV2E))
 
 
-def _fl_pair(precision, nsteps=300, T=400.0):
+def _fl_pair(precision, nsteps=300, T=400.0, lanes=None):
     x0, box = I.diamond(2, 2, 2)
     v0 = I.gaussian_velocities(len(x0), _sv(T), 1)
     orc = O.System(x=x0.copy(), v=v0.copy(), box=box.copy(), r0=x0.copy(), k_E=5.0, T=T, tdamp=0.1,
@@ -184,6 +184,8 @@ def _fl_pair(precision, nsteps=300, T=400.0):
     s = ctx.add_system(x0, box, v=v0, r0=x0)
     ctx.set_thermostat(s, T, 0.1, 9)
     ctx.set_schedule(s, nefe.NEFE_SCHED_FL, direction=1, nsteps=1000, k_E=5.0)
+    if lanes is not None:
+        ctx.set_tuning(lanes)
     ctx.run(nsteps)
     res = ctx.results(s)
     x, v, _ = ctx.get_state(s)
@@ -204,8 +206,9 @@ def test_frenkel_ladd_trajectory_fp64_matches_oracle(N):
     assert res["T"] == pytest.approx(ro["T"], rel=1e-7)
 
 
-def test_frenkel_ladd_trajectory_fp32_close_to_oracle(N):
-    orc, res, x, v = _fl_pair(0, nsteps=100)
+@pytest.mark.parametrize("lanes", [1, 4, 8, 32])
+def test_frenkel_ladd_trajectory_fp32_close_to_oracle(N, lanes):
+    orc, res, x, v = _fl_pair(0, nsteps=100, lanes=lanes)
     ro = orc.results()
     assert np.abs(x - orc.x).max() < 1e-4
     assert res["W"] == pytest.approx(ro["W"], rel=1e-3, abs=1e-3)
