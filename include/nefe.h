@@ -175,6 +175,25 @@ NEFE_API int nefe_sw_forces(const double* x, int n, const double box[3], double 
                    int* shell_overflow, void* stream);
 
 /*
+ * nefe_sw_energy_grad - the SW energy, forces and the derivatives of the energy with respect to
+ * the potential parameters theta = (A, B, p, q, a, lambda3, gamma) (eps, sigma, cos0 fixed), for
+ * differentiating the model (the backward of an energy function).  Pair terms give
+ *   dE/dA = E2/A, dE/dB = eps A s^-p e, dE/dp = -eps A B s^-p ln(s) e, dE/dq = eps A s^-q ln(s) e,
+ *   dE/da = sum phi2/(s-a)^2 + sum h gamma (1/(s_ij-a)^2 + 1/(s_ik-a)^2)
+ * with e = exp(1/(s-a)); triplet terms dE/dlambda3 = sum h/lambda3, dE/dgamma =
+ * sum h (1/(s_ij-a) + 1/(s_ik-a)).  Same list and layout rules as nefe_sw_forces.
+ *   f            device out FP64 SoA [3n] forces, or NULL.
+ *   energy_grad  device out FP64 [8]: E, then dE/dA, dE/dB, dE/dp, dE/dq, dE/da, dE/dlambda3,
+ *                dE/dgamma (each summed in fixed point, decoded in FP64).
+ * Returns NEFE_EOVERFLOW when an atom has more than 32 neighbours inside a*sigma, NEFE_ENAN on
+ * a non-finite sum, NEFE_EINVAL on bad arguments, NEFE_ENOMEM / NEFE_ECUDA.  Blocking: yes (it reads the
+ * error word back).
+ */
+NEFE_API int nefe_sw_energy_grad(const double* x, int n, const double box[3], double rcs,
+                                 const int* nbr, const int* cnt, int cap, const nefe_sw_params* prm,
+                                 int precision, double* f, double* energy_grad, void* stream);
+
+/*
  * nefe_langevin_noise - the standard-normal thermostat noise the integrator draws for
  * atoms 0..n-1 of system `sys_id` at step `step`: Philox4x64-10 (Salmon et al., SC'11) with
  * counter (step, atom, sys_id, 0) and key (seed, 0), two Box-Muller pairs from the four
@@ -346,6 +365,79 @@ NEFE_API int nefe_get_profile(nefe_ctx* ctx, double* us, long* samples);
 
 /* Number of kernel launches the context issued so far (for launch accounting). */
 NEFE_API int nefe_launch_count(nefe_ctx* ctx, long* count);
+
+/* ------------------------------------------------------------------------------------------
+ * Differentiation of the switching work (the W adjoint).
+ *
+ * W(theta) = sum_k dH/dlambda(x_k) (lambda_{k+1} - lambda_k) (Eq. Wdyn, left point) along an
+ * FP64 NVT Langevin velocity-Verlet trajectory (Frenkel-Ladd: dH/dlambda = U_E - U_SW, Sec. 2.1;
+ * reversible scaling: dH/dlambda = U_SW + P V, Sec. 2.2), as a function of the SW parameters
+ * theta = (A, B, p, q, a, lambda3, gamma) and of the initial state, with the thermostat noise
+ * (same Philox stream as the engine) held fixed.  The update is the engine's: half kick, drift,
+ * F = s_int F_SW + s_E F_E - (m/tdamp) v_half + amp (xi - mean xi), half kick.
+ * ------------------------------------------------------------------------------------------ */
+
+/*
+ * nefe_sw_dual - SW energy, forces and dU/dtheta in FP64 dual numbers: the dual direction is
+ * the displacement w of every atom together with the parameter direction dtheta.  Gives the
+ * Hessian-vector product J w (J = dF/dx) and the mixed product (d2U/dtheta dx) w.
+ *   x, w      device in FP64 SoA [3n] (w may be NULL: zero)
+ *   nbr, cnt  a list from nefe_neighbor_build with rcs >= a*sigma (minimum image is taken on
+ *             the box, so box >= 2 rcs as there)
+ *   dtheta    host [7] parameter direction, or NULL (zero)
+ *   f, fd     device out FP64 SoA [3n]: F and its dual part J w + (dF/dtheta) dtheta
+ *   out16     device out FP64 [16]: E, E' = -F.w + G.dtheta, G = dU/dtheta [7], G' [7]
+ * Returns NEFE_EOVERFLOW (shell above 32), NEFE_ENAN, NEFE_EINVAL, NEFE_ECUDA.  Blocking: yes.
+ */
+NEFE_API int nefe_sw_dual(const double* x, const double* w, int n, const double box[3], double rcs,
+                          const int* nbr, const int* cnt, int cap, const nefe_sw_params* prm,
+                          const double* dtheta, double* f, double* fd, double* out16, void* stream);
+
+typedef struct nefe_adj nefe_adj;
+
+typedef struct nefe_adjoint_desc {
+    int n;                     /* atoms                                                     */
+    const double* x;           /* host (n, 3) initial positions, A (copied at create)       */
+    const double* v;           /* host (n, 3) initial velocities, A/ps                      */
+    const double* r0;          /* host (n, 3) Einstein sites (FL), or NULL (RS)             */
+    double box[3];             /* orthorhombic periodic box, A (fixed: NVT), >= 2 rcs       */
+    double mass;               /* g/mol                                                     */
+    double dt;                 /* ps                                                        */
+    double T;                  /* K                                                         */
+    double tdamp;              /* ps; <= 0: no thermostat                                   */
+    uint64_t seed, sys_id;     /* noise stream                                              */
+    int kind;                  /* NEFE_SCHED_FL or NEFE_SCHED_RS                            */
+    int direction;             /* +1 forward, -1 backward                                   */
+    long nsched;               /* switching steps: tau = min(k / nsched, 1)                 */
+    double k_E;                /* FL spring, eV/A^2                                         */
+    double lambda_f;           /* RS end point                                              */
+    double P_GPa;              /* RS: external pressure in the P V term                     */
+    double skin;               /* list radius rcs = a sigma + skin, A                       */
+    int nbr_cap;               /* neighbour row capacity, 1..64                             */
+    int checkpoint_every;      /* K_c: (x, v, F) kept every K_c steps, >= 1                 */
+} nefe_adjoint_desc;
+
+/* Creates the context on `device` / `stream` (device memory ~ (17 + 3 K_c) n doubles plus
+ * 9 n doubles per checkpoint).  NEFE_EINVAL on bad arguments, NEFE_ENOMEM. */
+NEFE_API int nefe_adjoint_create(nefe_adj** out, int device, void* stream, const nefe_adjoint_desc* desc,
+                                 const nefe_sw_params* prm);
+NEFE_API int nefe_adjoint_destroy(nefe_adj* adj);
+/* Replaces the SW parameters (a*sigma must stay within the list radius fixed at create);
+ * invalidates the checkpoints. */
+NEFE_API int nefe_adjoint_set_params(nefe_adj* adj, const nefe_sw_params* prm);
+/* Runs nsteps from the initial state, keeping the checkpoints; *W (host) = the work.  The neighbour
+ * list is rebuilt at every force evaluation.  Blocking.  NEFE_EOVERFLOW / NEFE_ENAN on a bad run. */
+NEFE_API int nefe_adjoint_forward(nefe_adj* adj, long nsteps, double* W);
+/* Reverse sweep over the last forward run: dW/dtheta (host [7]) and, when not NULL, dW/dx0 and
+ * dW/dv0 (host (n, 3)).  Each segment is recomputed from its checkpoint.  Blocking.
+ * NEFE_ESTATE without a preceding forward run. */
+NEFE_API int nefe_adjoint_backward(nefe_adj* adj, double dW_dtheta[7], double* dW_dx0, double* dW_dv0);
+/* Tangent-linear run: W and its directional derivative dW along (dtheta [7], dx0, dv0 (n, 3) host
+ * or NULL).  Invalidates the checkpoints.  Blocking. */
+NEFE_API int nefe_adjoint_tangent(nefe_adj* adj, long nsteps, const double dtheta[7], const double* dx0,
+                                  const double* dv0, double* W, double* dW);
+/* Positions and velocities (host (n, 3), either may be NULL) at the end of the last run. */
+NEFE_API int nefe_adjoint_state(nefe_adj* adj, double* x, double* v);
 
 #ifdef __cplusplus
 }

@@ -18,8 +18,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnefe.so")
-SOURCES = ["nefe_kernels.cu", "nefe_api.cu", "nefe_engine.cu", "nefe_noalloc.cu"]
+SOURCES = ["nefe_kernels.cu", "nefe_api.cu", "nefe_engine.cu", "nefe_noalloc.cu", "nefe_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The adjoint unit is built without FMA contraction, so the real parts of its dual-number
+# kernel round exactly like its plain FP64 kernel (identical trajectories in the forward, the
+# tangent-linear and the recomputed runs).
+EXTRA = {"nefe_adjoint.cu": ["-fmad=false"]}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]
 
@@ -54,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -36,42 +36,7 @@ bool valid_params(const nefe_sw_params* p) {
            std::isfinite(p->lambda3) && std::isfinite(p->gamma) && std::isfinite(p->cos0);
 }
 
-// Temporary single-system descriptors for the stateless calls.
-struct Scratch1 {
-    DevSys* sys = nullptr;
-    DevState* st = nullptr;
-    int* tile_sys = nullptr;
-    long long* acc = nullptr;
-    void* swc = nullptr;
-    int4* q = nullptr;
-    void* xs = nullptr;
-    void* xa = nullptr;
-    void* shd = nullptr;
-    int* shj = nullptr;
-    int* shn = nullptr;
-    void* P = nullptr;
-    int* cell_of = nullptr;
-    int* perm = nullptr;
-    int* cell_start = nullptr;
-    int* cell_count = nullptr;
-    int* cell_cursor = nullptr;
-    cudaStream_t s = nullptr;
-    std::vector<void*> owned;
-
-    template <typename P>
-    cudaError_t alloc(P** p, size_t bytes) {
-        void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, s);
-        if (e == cudaSuccess) owned.push_back(q);
-        *p = static_cast<P*>(q);
-        return e;
-    }
-    ~Scratch1() {
-        for (void* p : owned) cudaFreeAsync(p, s);
-    }
-};
-
-static int check_box(const double box[3], double rcs) {
+int check_box(const double box[3], double rcs) {
     for (int k = 0; k < 3; ++k)
         if (!(box[k] > 0.0) || !std::isfinite(box[k]))
             return fail(NEFE_EINVAL, "box length %d is not positive and finite", k);
@@ -82,8 +47,7 @@ static int check_box(const double box[3], double rcs) {
     return NEFE_OK;
 }
 
-// Sets up the one-system descriptors, the tile table and the cell arrays.
-static int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap, int prec,
+int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap, int prec,
                     bool cells) {
     const int ntiles = (n + kTile - 1) / kTile;
     DevSys hs;
@@ -120,7 +84,7 @@ static int prepare1(Scratch1& S, int n, const double box[3], double rcs, int nce
     return NEFE_OK;
 }
 
-static Bufs bufs_of(const Scratch1& S, const double* x, int n) {
+Bufs bufs_of(const Scratch1& S, const double* x, int n) {
     Bufs b;
     std::memset(&b, 0, sizeof(b));
     b.sys = S.sys; b.st = S.st; b.acc = S.acc; b.tile_sys = S.tile_sys;
@@ -255,6 +219,59 @@ int nefe_sw_forces(const double* x, int n, const double box[3], double rcs, cons
         *shell_overflow = (st.err & NEFE_ERR_SHELL_OVERFLOW) ? 1 : 0;
         if (*shell_overflow) return fail(NEFE_EOVERFLOW, "nefe_sw_forces: shell above 32 neighbours");
     }
+    return NEFE_OK;
+}
+
+int nefe_sw_energy_grad(const double* x, int n, const double box[3], double rcs, const int* nbr,
+                        const int* cnt, int cap, const nefe_sw_params* prm, int precision, double* f,
+                        double* energy_grad, void* stream) {
+    if (n < 0 || !box || cap < 1 || cap > kMaxCap || !valid_params(prm) || !energy_grad ||
+        (precision != NEFE_FP32 && precision != NEFE_FP64) || (n > 0 && (!x || !nbr || !cnt)))
+        return fail(NEFE_EINVAL, "nefe_sw_energy_grad: bad argument");
+    if (prm->a * prm->sigma > rcs) return fail(NEFE_EINVAL, "nefe_sw_energy_grad: a*sigma above rcs");
+    int rc = check_box(box, rcs);
+    if (rc) return rc;
+    int n3[3];
+    if (!host_grid(box, rcs, n3)) return fail(NEFE_EINVAL, "nefe_sw_energy_grad: fewer than 2 cells on an axis");
+    const long long total = (long long)n3[0] * n3[1] * n3[2];
+    Scratch1 S;
+    S.s = (cudaStream_t)stream;
+    rc = prepare1(S, n, box, rcs, (int)(total > (1LL << 30) ? (1LL << 30) : total), precision, false);
+    if (rc) return rc;
+    if (precision == NEFE_FP64) {
+        SWc<double> c = make_swc<double>(*prm);
+        NEFE_CU(S.alloc(&S.swc, sizeof(c)));
+        NEFE_CU(cudaMemcpyAsync(S.swc, &c, sizeof(c), cudaMemcpyHostToDevice, S.s));
+    } else {
+        SWc<float> c = make_swc<float>(*prm);
+        NEFE_CU(S.alloc(&S.swc, sizeof(c)));
+        NEFE_CU(cudaMemcpyAsync(S.swc, &c, sizeof(c), cudaMemcpyHostToDevice, S.s));
+    }
+    if (n > 0) {
+        const size_t v4 = precision == NEFE_FP64 ? sizeof(double4) : sizeof(float4);
+        double* fo = f;
+        if (!fo) NEFE_CU(S.alloc(&fo, sizeof(double) * 3 * (size_t)n));
+        NEFE_CU(S.alloc(&S.shd, v4 * (size_t)n * kShell));
+        NEFE_CU(S.alloc(&S.shj, sizeof(int) * (size_t)n * kShell));
+        NEFE_CU(S.alloc(&S.shn, sizeof(int) * (size_t)n));
+        NEFE_CU(S.alloc(&S.P, v4 * (size_t)n));
+        Bufs b = bufs_of(S, x, n);
+        b.nbr = const_cast<int*>(nbr); b.cnt = const_cast<int*>(cnt); b.cap = cap;
+        b.f_out = fo; b.e_atom = nullptr; b.want_grad = 1;
+        const int ntiles = (n + kTile - 1) / kTile;
+        launch_mirror(b, precision, ntiles, S.s, nullptr);
+        launch_edges(b, precision, 8, ntiles, FM_FORCES, S.s, nullptr);
+        launch_gather(b, precision, 4, ntiles, FM_FORCES, S.s, nullptr);
+        NEFE_CU(cudaGetLastError());
+    }
+    launch_decode_grad(S.acc, energy_grad, S.s);
+    NEFE_CU(cudaGetLastError());
+    DevState st;
+    NEFE_CU(cudaMemcpyAsync(&st, S.st, sizeof(st), cudaMemcpyDeviceToHost, S.s));
+    NEFE_CU(cudaStreamSynchronize(S.s));
+    if (st.err & NEFE_ERR_SHELL_OVERFLOW)
+        return fail(NEFE_EOVERFLOW, "nefe_sw_energy_grad: shell above 32 neighbours");
+    if (st.err & NEFE_ERR_NAN) return fail(NEFE_ENAN, "nefe_sw_energy_grad: non-finite sum");
     return NEFE_OK;
 }
 

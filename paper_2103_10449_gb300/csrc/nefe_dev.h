@@ -25,7 +25,8 @@ enum Acc {
     ACC_VIR,            // 6: SW virial xx yy zz xy xz yz (unscaled)
     ACC_KT = ACC_VIR + 6,   // 6: sum m v_a v_b (eV)
     ACC_XI = ACC_KT + 6,    // 3: sum of thermostat normals of the current step
-    ACC_N = ACC_XI + 3
+    ACC_DTH = ACC_XI + 3,   // 7: dE/d(A, B, p, q, a, lambda3, gamma) (stateless gradient call)
+    ACC_N = ACC_DTH + 7
 };
 
 enum Sched { SCHED_NONE = 0, SCHED_FL = 1, SCHED_RS = 2, SCHED_AS = 3 };
@@ -43,6 +44,7 @@ struct SWc {
     T epslam;      // eps * lambda3
     T gam;
     T c0;
+    T eps, A, lam3;  // for the parameter derivatives
     T s_act;       // edges with r/sigma >= s_act are dropped (see make_swc)
     T act2;        // (s_act sigma)^2
     int int_pq;    // 1 when p == 4 and q == 0 (the standard set): s^-p by multiplications

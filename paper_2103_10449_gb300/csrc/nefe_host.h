@@ -2,9 +2,11 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cmath>
+#include <vector>
 
 #include "nefe.h"
 #include "nefe_dev.h"
+#include "nefe_launch.h"
 
 namespace nefe {
 
@@ -46,6 +48,9 @@ inline SWc<T> make_swc(const nefe_sw_params& p) {
     c.epslam = (T)(p.eps * p.lambda3);
     c.gam = (T)p.gamma;
     c.c0 = (T)p.cos0;
+    c.eps = (T)p.eps;
+    c.A = (T)p.A;
+    c.lam3 = (T)p.lambda3;
     // FP32 path: an edge whose three-body factor exp(gamma/(s - a)) is below 1e-12 adds forces
     // of order 1e-8 eV/A (pair and triplet), far below FP32 resolution, so it is dropped:
     // s_act = a + gamma / ln(1e-12).  FP64 path: only the last 1e-12 sigma before the cutoff
@@ -59,5 +64,48 @@ inline SWc<T> make_swc(const nefe_sw_params& p) {
 }
 
 bool valid_params(const nefe_sw_params* p);
+
+// Single-system descriptors and scratch for the stateless calls and the adjoint context
+// (stream-ordered allocations, released on the same stream).
+struct Scratch1 {
+    DevSys* sys = nullptr;
+    DevState* st = nullptr;
+    int* tile_sys = nullptr;
+    long long* acc = nullptr;
+    void* swc = nullptr;
+    int4* q = nullptr;
+    void* xs = nullptr;
+    void* xa = nullptr;
+    void* shd = nullptr;
+    int* shj = nullptr;
+    int* shn = nullptr;
+    void* P = nullptr;
+    int* cell_of = nullptr;
+    int* perm = nullptr;
+    int* cell_start = nullptr;
+    int* cell_count = nullptr;
+    int* cell_cursor = nullptr;
+    cudaStream_t s = nullptr;
+    std::vector<void*> owned;
+
+    template <typename P>
+    cudaError_t alloc(P** p, size_t bytes) {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, bytes < 16 ? 16 : bytes, s);
+        if (e == cudaSuccess) owned.push_back(q);
+        *p = static_cast<P*>(q);
+        return e;
+    }
+    ~Scratch1() {
+        for (void* p : owned) cudaFreeAsync(p, s);
+    }
+};
+
+// NEFE_OK when every box length is positive, finite and at least 2 rcs.
+int check_box(const double box[3], double rcs);
+// Sets up the one-system descriptors, the tile table and (cells) the cell arrays.
+int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap, int prec, bool cells);
+// Launch arguments over S for n atoms at FP64 positions x.
+Bufs bufs_of(const Scratch1& S, const double* x, int n);
 
 }  // namespace nefe

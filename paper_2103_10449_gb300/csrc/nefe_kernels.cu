@@ -48,6 +48,8 @@ __device__ __forceinline__ double xrcp(double v) { return 1.0 / v; }
 __device__ __forceinline__ float xrsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double xrsqrt(double v) { return ::rsqrt(v); }
 __device__ __forceinline__ float xpow(float a, float b) { return __powf(a, b); }
+__device__ __forceinline__ float xlog(float v) { return __logf(v); }
+__device__ __forceinline__ double xlog(double v) { return ::log(v); }
 __device__ __forceinline__ double xpow(double a, double b) { return ::pow(a, b); }
 
 // FP32 copy or FP64 source of a constant, by kernel precision.
@@ -679,6 +681,28 @@ __device__ __forceinline__ void sw_edge(const SWc<T>& P, T r, T& phi, T& dphi, T
     dg = -g * P.gam * id * id * P.inv_sig;
 }
 
+// Derivatives of one pair term phi2(r) with respect to A, B, p, q, a (sigma, eps fixed):
+// phi2 = eps A (B s^-p - s^-q) e,  e = exp(1/(s - a)).
+template <typename T>
+__device__ __forceinline__ void sw_pair_pgrad(const SWc<T>& P, T r, T out[5]) {
+    const T s = r * P.inv_sig;
+    if (!(s < P.s_act) || !(s - P.a < -cut_eps<T>())) {
+        for (int k = 0; k < 5; ++k) out[k] = (T)0;
+        return;
+    }
+    const T id = xrcp(s - P.a);
+    const T e1 = xexp(id);
+    const T ls = xlog(s);
+    const T rp = xpow(s, -P.p), rq = xpow(s, -P.q);
+    const T ea = P.eps * P.A * e1;
+    const T phi = ea * (P.B * rp - rq);
+    out[0] = phi / P.A;                 // d/dA
+    out[1] = ea * rp;                   // d/dB
+    out[2] = -ea * P.B * rp * ls;       // d/dp
+    out[3] = ea * rq * ls;              // d/dq
+    out[4] = phi * id * id;             // d/da (pair exponent)
+}
+
 // Force pass A.  L lanes per atom, 128/L atoms per block, the in-cutoff shell staged in
 // shared memory and also stored compactly (d_ij and g_ij per entry, neighbour index) for
 // pass B.  Pair terms on the lanes that find the edge; triplets (i; a, b), a < b, dealt
@@ -691,6 +715,7 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     __shared__ T4 sh_d[G][kShell];
     __shared__ T sh_g[G][kShell];
     __shared__ T sh_dg[G][kShell];
+    __shared__ T sh_id[G][kShell];
 
     const int tile = blockIdx.x / L + b.tile_base, part = blockIdx.x % L;
     const TileAtom ta = tile_of(b, tile);
@@ -709,6 +734,8 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
 
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    T gth[7] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};   // dE/d(A, B, p, q, a, lambda3, gamma)
+    const bool grad = b.want_grad != 0;
     if (valid) {
         const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
         const int ci = min(b.cnt[i], b.cap);
@@ -744,6 +771,13 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
                     sh_dg[grp][pos] = dg;
                     Sd[pos] = mk4(dx, dy, dz, g);
                     Sj[pos] = j;
+                    if (grad) {   // each pair is seen from both ends: half of each derivative
+                        T pg[5];
+                        sw_pair_pgrad<T>(P, r, pg);
+                        for (int k = 0; k < 5; ++k) gth[k] += (T)0.5 * pg[k];
+                        const T den = r * P.inv_sig - P.a;
+                        sh_id[grp][pos] = den < -cut_eps<T>() ? xrcp(den) : (T)0;
+                    }
                     const T c = dphi * xrcp(r);
                     fx += c * dx; fy += c * dy; fz += c * dz;
                     en += (T)0.5 * phi;
@@ -787,6 +821,13 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
                     const T fbz = -(tb_ * (uaz - c * ubz) + dc2 * ga * dgb * ubz);
                     fx -= fax + fbx; fy -= fay + fby; fz -= faz + fbz;
                     en += dc2 * ga * gb;
+                    if (grad) {
+                        const T hh = dc2 * ga * gb;
+                        const T ia_ = sh_id[grp][a], ib_ = sh_id[grp][bb];
+                        gth[4] += hh * P.gam * (ia_ * ia_ + ib_ * ib_);
+                        gth[5] += P.eps * dc * dc * ga * gb;
+                        gth[6] += hh * (ia_ + ib_);
+                    }
                     w0 += da.x * fax + db.x * fbx;
                     w1 += da.y * fay + db.y * fby;
                     w2 += da.z * faz + db.z * fbz;
@@ -812,6 +853,7 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     }
     T red[8] = {en, (T)0, w0, w1, w2, w3, w4, w5};
     block_sum_to_acc<T, 8>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    if (grad) block_sum_to_acc<T, 7>(gth, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_DTH, &st.err);
 }
 
 // Force pass A, one thread per atom (64-thread blocks, half a tile each).  The row is first
@@ -1401,6 +1443,19 @@ void launch_aos_soa(const double* src, double* dst, int n, int to_soa, cudaStrea
     const int blocks = (3 * n + 255) / 256;
     if (to_soa) k_aos_to_soa<<<blocks, 256, 0, s>>>(src, dst, n);
     else k_soa_to_aos<<<blocks, 256, 0, s>>>(src, dst, n);
+}
+
+__global__ void k_decode_grad(const long long* acc, double* out8) {
+    const int t = threadIdx.x;
+    if (t >= 8) return;
+    const int a = t == 0 ? ACC_UINT : ACC_DTH + (t - 1);
+    long long sum = 0;
+    for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)a * kSlots + sl];
+    out8[t] = (double)sum / kFix;
+}
+
+void launch_decode_grad(const long long* acc, double* out8, cudaStream_t s) {
+    k_decode_grad<<<1, 32, 0, s>>>(acc, out8);
 }
 
 void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s) {

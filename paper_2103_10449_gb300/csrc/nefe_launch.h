@@ -47,6 +47,7 @@ struct Bufs {
     double* trace;
     double* f_out;           // stateless: FP64 SoA forces
     double* e_atom;          // stateless: per-atom energy (may be NULL)
+    int want_grad;           // pass A also sums dE/d(A, B, p, q, a, lambda3, gamma)
 };
 
 enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };
@@ -56,6 +57,8 @@ void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_
                   cudaStream_t s, long* launches);
 // Decodes one system's fixed-point sums into [U_int, virial xx yy zz xy xz yz] (FP64, device).
 void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s);
+// Decodes [U_int, dE/dA, dE/dB, dE/dp, dE/dq, dE/da, dE/dlambda3, dE/dgamma] (FP64, device).
+void launch_decode_grad(const long long* acc, double* out8, cudaStream_t s);
 // Rebuild sequence (only systems whose rebuild flag is set, or all when force_all).
 void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
                            cudaStream_t s, long* launches);

@@ -50,6 +50,17 @@ class nefe_schedule(ctypes.Structure):
                 ("P0_GPa", ctypes.c_double), ("P1_GPa", ctypes.c_double), ("lambda0", ctypes.c_double)]
 
 
+class nefe_adjoint_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("x", ctypes.POINTER(ctypes.c_double)),
+                ("v", ctypes.POINTER(ctypes.c_double)), ("r0", ctypes.POINTER(ctypes.c_double)),
+                ("box", ctypes.c_double * 3), ("mass", ctypes.c_double), ("dt", ctypes.c_double),
+                ("T", ctypes.c_double), ("tdamp", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("sys_id", ctypes.c_uint64), ("kind", ctypes.c_int), ("direction", ctypes.c_int),
+                ("nsched", ctypes.c_long), ("k_E", ctypes.c_double), ("lambda_f", ctypes.c_double),
+                ("P_GPa", ctypes.c_double), ("skin", ctypes.c_double), ("nbr_cap", ctypes.c_int),
+                ("checkpoint_every", ctypes.c_int)]
+
+
 class nefe_results(ctypes.Structure):
     _fields_ = [("W", ctypes.c_double), ("lambda_", ctypes.c_double), ("step", ctypes.c_long),
                 ("U", ctypes.c_double), ("U_E", ctypes.c_double), ("K", ctypes.c_double),
@@ -81,6 +92,18 @@ SIGNATURES = {
     "nefe_neighbor_build": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, ctypes.c_int, _vp, _vp, _c_int_p, _vp],
     "nefe_sw_forces": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
                        ctypes.POINTER(nefe_sw_params), ctypes.c_int, _vp, _vp, _vp, _c_int_p, _vp],
+    "nefe_sw_energy_grad": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
+                            ctypes.POINTER(nefe_sw_params), ctypes.c_int, _vp, _vp, _vp],
+    "nefe_sw_dual": [_vp, _vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
+                     ctypes.POINTER(nefe_sw_params), _c_dbl_p, _vp, _vp, _vp, _vp],
+    "nefe_adjoint_create": [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(nefe_adjoint_desc),
+                            ctypes.POINTER(nefe_sw_params)],
+    "nefe_adjoint_destroy": [_vp],
+    "nefe_adjoint_set_params": [_vp, ctypes.POINTER(nefe_sw_params)],
+    "nefe_adjoint_forward": [_vp, ctypes.c_long, _c_dbl_p],
+    "nefe_adjoint_backward": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "nefe_adjoint_tangent": [_vp, ctypes.c_long, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "nefe_adjoint_state": [_vp, _c_dbl_p, _c_dbl_p],
     "nefe_langevin_noise": [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _vp, _vp],
     "nefe_create": [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int],
     "nefe_destroy": [_vp],
@@ -155,9 +178,12 @@ def _ptr(t):
 
 
 def _stream(stream):
+    """cudaStream_t of a torch stream, a raw handle (int) or the current torch stream (None)."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
 
 
@@ -211,6 +237,18 @@ def nefe_sw_forces(x, n, box, rcs, nbr, cnt, cap, prm, precision, f, e_atom=None
                                  ctypes.byref(prm), int(precision), _ptr(f), _ptr(e_atom),
                                  _ptr(energy_virial), ctypes.byref(ovf), _stream(stream)))
     return ovf.value
+
+
+def nefe_sw_energy_grad(x, n, box, rcs, nbr, cnt, cap, prm, precision, f, energy_grad, stream=None):
+    _check(load().nefe_sw_energy_grad(_ptr(x), int(n), _box(box), float(rcs), _ptr(nbr), _ptr(cnt), int(cap),
+                                      ctypes.byref(prm), int(precision), _ptr(f), _ptr(energy_grad),
+                                      _stream(stream)))
+
+
+def nefe_sw_dual(x, w, n, box, rcs, nbr, cnt, cap, prm, dtheta, f, fd, out16, stream=None):
+    dth = None if dtheta is None else (ctypes.c_double * 7)(*[float(v) for v in dtheta])
+    _check(load().nefe_sw_dual(_ptr(x), _ptr(w), int(n), _box(box), float(rcs), _ptr(nbr), _ptr(cnt), int(cap),
+                               ctypes.byref(prm), dth, _ptr(f), _ptr(fd), _ptr(out16), _stream(stream)))
 
 
 def nefe_langevin_noise(seed, sys_id, step, n, precision, xi, stream=None):
@@ -371,3 +409,83 @@ class Context:
         c = ctypes.c_long(0)
         _check(self._L.nefe_launch_count(self.h, ctypes.byref(c)))
         return c.value
+
+
+def _host_aos(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(n, 3)
+    return a
+
+
+class Adjoint:
+    """Switching work W(theta) of one FP64 NVT switching run and its derivatives (adjoint sweep
+    over checkpointed segments, or a tangent-linear run) through the C ABI."""
+
+    def __init__(self, x, v, box, prm=None, kind=NEFE_SCHED_FL, r0=None, direction=1, nsched=1000,
+                 k_E=5.0, lambda_f=1.0, P_GPa=0.0, T=400.0, tdamp=0.1, seed=1, sys_id=0, mass=28.0855,
+                 dt=0.001, skin=0.5, nbr_cap=48, checkpoint_every=45, device=0, stream=None):
+        self.n = len(x)
+        self._x = _host_aos(x, self.n)
+        self._v = _host_aos(v, self.n)
+        self._r0 = None if r0 is None else _host_aos(r0, self.n)
+        d = nefe_adjoint_desc()
+        d.n = self.n
+        d.x = self._x.ctypes.data_as(_c_dbl_p)
+        d.v = self._v.ctypes.data_as(_c_dbl_p)
+        d.r0 = None if self._r0 is None else self._r0.ctypes.data_as(_c_dbl_p)
+        d.box[:] = [float(b) for b in box]
+        d.mass, d.dt, d.T, d.tdamp = float(mass), float(dt), float(T), float(tdamp)
+        d.seed, d.sys_id, d.kind, d.direction, d.nsched = int(seed), int(sys_id), int(kind), int(direction), int(nsched)
+        d.k_E, d.lambda_f, d.P_GPa, d.skin = float(k_E), float(lambda_f), float(P_GPa), float(skin)
+        d.nbr_cap, d.checkpoint_every = int(nbr_cap), int(checkpoint_every)
+        self.prm = nefe_sw_params_silicon() if prm is None else (prm if isinstance(prm, nefe_sw_params) else params_from(prm))
+        self._h = _vp()
+        _check(load().nefe_adjoint_create(ctypes.byref(self._h), int(device), _stream(stream), ctypes.byref(d),
+                                          ctypes.byref(self.prm)))
+
+    def close(self):
+        if self._h:
+            load().nefe_adjoint_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, prm):
+        self.prm = prm if isinstance(prm, nefe_sw_params) else params_from(prm)
+        _check(load().nefe_adjoint_set_params(self._h, ctypes.byref(self.prm)))
+
+    def forward(self, nsteps):
+        W = ctypes.c_double(0.0)
+        _check(load().nefe_adjoint_forward(self._h, int(nsteps), ctypes.byref(W)))
+        return W.value
+
+    def backward(self, initial_state=False):
+        g = (ctypes.c_double * 7)()
+        if initial_state:
+            gx = np.zeros((self.n, 3))
+            gv = np.zeros((self.n, 3))
+            _check(load().nefe_adjoint_backward(self._h, g, gx.ctypes.data_as(_c_dbl_p), gv.ctypes.data_as(_c_dbl_p)))
+            return np.array(g[:]), gx, gv
+        _check(load().nefe_adjoint_backward(self._h, g, None, None))
+        return np.array(g[:])
+
+    def tangent(self, nsteps, dtheta, dx0=None, dv0=None):
+        dth = (ctypes.c_double * 7)(*[float(v) for v in dtheta])
+        ax = None if dx0 is None else _host_aos(dx0, self.n)
+        av = None if dv0 is None else _host_aos(dv0, self.n)
+        W = ctypes.c_double(0.0)
+        dW = ctypes.c_double(0.0)
+        _check(load().nefe_adjoint_tangent(self._h, int(nsteps), dth,
+                                           None if ax is None else ax.ctypes.data_as(_c_dbl_p),
+                                           None if av is None else av.ctypes.data_as(_c_dbl_p),
+                                           ctypes.byref(W), ctypes.byref(dW)))
+        return W.value, dW.value
+
+    def state(self):
+        x = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        _check(load().nefe_adjoint_state(self._h, x.ctypes.data_as(_c_dbl_p), v.ctypes.data_as(_c_dbl_p)))
+        return x, v
