@@ -75,17 +75,18 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per atom of the force kernel from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_force_fl8000_traffic.txt")
+def recorded_traffic(kernel):
+    """DRAM bytes per atom of `kernel` from the committed ncu summary, if that summary was taken
+    on the current kernel source and for this kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "force_passes_traffic.txt")
     try:
         txt = open(path).read()
     except OSError:
         return None
+    k = re.search(r"^kernel:\s*(\w+)", txt, re.M)
     m = re.search(r"kernel_source_sha256_16:\s*(\w+)", txt)
     b = re.search(r"dram_bytes_per_atom:\s*([0-9.eE+-]+)", txt)
-    if not m or not b or m.group(1) != kernel_hash():
+    if not k or not m or not b or k.group(1) != kernel or m.group(1) != kernel_hash():
         return None
     return float(b.group(1))
 
@@ -153,6 +154,51 @@ def build_context(N, replicas, precision, seed0=1000, stream=None):
         ctx.set_schedule(s, N.NEFE_SCHED_FL, direction=1 if r % 2 == 0 else -1, nsteps=NSCHED, k_E=K_E)
     ctx.setup()
     return ctx, len(x)
+
+
+def free_energy_error(N, reps=8, n_eq=500, n_sw=2000):
+    """FP32 against FP64 free-energy estimate of the same switching experiment.
+
+    reps forward (SW -> Einstein) and reps backward (Einstein -> SW) Frenkel-Ladd realisations
+    of the 8000-atom crystal at 1000 K, n_sw steps each, from endpoint states equilibrated for
+    n_eq steps in FP64; both precisions start from identical states with identical noise
+    seeds.  Returns the switching part of the free energy, -1/2 (<W_f> - <W_b>)/N (the
+    Einstein reference term is the same for both and cancels in the error), per precision,
+    their difference and the standard error of the estimate itself."""
+    from paper_2103_10449_gb300 import inputs as I
+    x, box = I.diamond(NCELL, NCELL, NCELL)
+    n = len(x)
+    sv = math.sqrt(KB * T_SW / (MASS * MVV2E))
+    eq = N.Context(precision=N.NEFE_FP64, dt=0.001, skin=0.5, nbr_cap=48)
+    for r in range(2 * reps):
+        fwd = r < reps
+        s = eq.add_system(x, box, v=I.gaussian_velocities(n, sv, 5000 + r), r0=x, mass=MASS,
+                          pot=N.NEFE_POT_SW if fwd else N.NEFE_POT_EINSTEIN, k_int=0.0 if fwd else K_E)
+        eq.set_thermostat(s, T_SW, 0.1, 5000 + r)
+    eq.run(n_eq)
+    states = [eq.get_state(r)[:2] for r in range(2 * reps)]
+    eq.close()
+    out = {}
+    for name, prec in (("fp64", N.NEFE_FP64), ("fp32", N.NEFE_FP32)):
+        c = N.Context(precision=prec, dt=0.001, skin=0.5, nbr_cap=48)
+        for r in range(2 * reps):
+            s = c.add_system(states[r][0], box, v=states[r][1], r0=x, mass=MASS)
+            c.set_thermostat(s, T_SW, 0.1, 7000 + r)
+            c.set_schedule(s, N.NEFE_SCHED_FL, direction=1 if r < reps else -1, nsteps=n_sw, k_E=K_E)
+        c.run(n_sw)
+        res = c.results_all()
+        c.close()
+        wf = np.array([res[r]["W"] for r in range(reps)])
+        wb = np.array([res[r]["W"] for r in range(reps, 2 * reps)])
+        out[name] = (-0.5 * (wf.mean() - wb.mean()) / n,
+                     0.5 * math.sqrt(wf.var(ddof=1) / reps + wb.var(ddof=1) / reps) / n,
+                     sum(int(r["error"] != 0) for r in res))
+    return {"dF_switch_fp64_eV_per_atom": out["fp64"][0], "dF_switch_fp32_eV_per_atom": out["fp32"][0],
+            "dG_err_meV_per_atom": 1000.0 * (out["fp32"][0] - out["fp64"][0]),
+            "stat_err_meV_per_atom": 1000.0 * out["fp64"][1],
+            "protocol": f"{reps} forward + {reps} backward FL realisations, {n_sw} steps each, 8000 atoms, 1000 K,"
+                        f" identical initial states and noise seeds in both precisions",
+            "systems_with_errors": out["fp64"][2] + out["fp32"][2]}
 
 
 def time_steps(torch, ctx, stream, steps, md_steps):
@@ -283,12 +329,12 @@ def main():
     # roofline of the dominant kernel (the longer force pass), from live CUDA-event durations
     bytes_a = PASS_A_FIXED + 4.0 * mean_cnt
     if b_us > a_us:
-        kname, kbytes, kus = "k_gather (force pass B: neighbour-centred triplets, springs, Langevin, kick)", PASS_B_BYTES, b_us
+        kkey, kname, kbytes, kus = "k_gather", "k_gather (force pass B: neighbour-centred triplets, springs, Langevin, kick)", PASS_B_BYTES, b_us
     else:
-        kname, kbytes, kus = "k_edges1 (force pass A: shell, pair terms, triplets centred on the atom)", bytes_a, a_us
+        kkey, kname, kbytes, kus = "k_edges1", "k_edges1 (force pass A: shell, pair terms, triplets centred on the atom)", bytes_a, a_us
     achieved = kbytes * atoms / (kus * 1e-6) / 1e9
     peak, peak_kind = peaks()
-    tr = recorded_traffic()
+    tr = recorded_traffic(kkey)
     step_gbs = value / world * STEP_BYTES / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None if tr is None else tr * atoms,
@@ -345,6 +391,7 @@ def main():
         comp["batched_fp32_over_fp64_single"] = value / world / comp["fp64_single_replica"]
         comp["batched_fp32_over_fp64_batched"] = value / world / comp["fp64_batched"]
         line["comparators"] = comp
+        line["dG_err"] = free_energy_error(N)
         cps, nst, dt = cpu_baseline_sample()
         line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{nst} FP64-oracle MD steps of one 8000-atom replica ({dt:.1f} s)"}
