@@ -41,13 +41,18 @@ T_SW = 1000.0
 K_E = 5.0
 NSCHED = 20000
 MD_STEPS = 32       # MD steps per timed step (one graph replay)
-# Algorithmic bytes per atom of the two force passes (FP32 path, Frenkel-Ladd):
-#   pass A (edges): own position 16 + row length 4 + neighbour row 4 nbar + partial force 16;
-#   pass B (gather): spring offset 16 + displacement 24 + noise 16 + v read 12 + v write 12
-#                    + total force write 16.
+SKIN = 0.7          # Verlet skin (A): fewest list builds for the least row growth at 1000 K (measured
+                    # over 0.5-1.1 A); it changes no result beyond the FP32 list band
+# Algorithmic bytes per atom of the two force passes (FP32 path, Frenkel-Ladd), m = mean
+# in-cutoff shell size, nbar = mean Verlet row length:
+#   pass A (edges): own mirror 16 + row length 4 + row 4 nbar + shell indices 4 m + leg forces
+#                   16 m + shell size 4 + partial force and energy 16;
+#   pass B (gather): partial force 16 + shell size 4 + own shell indices 4 m + the neighbours'
+#                    leg forces 16 m + spring offset 16 + displacement 24 + noise 16 + v read 12
+#                    + v write 12 + total force write 16.
 # Whole step (the method's minimum, FP64 x and v, r0, F, list): 212 B per atom-step.
-PASS_A_FIXED = 16 + 4 + 16
-PASS_B_BYTES = 16 + 24 + 16 + 12 + 12 + 16
+PASS_A_FIXED = 16 + 4 + 4 + 16
+PASS_B_FIXED = 16 + 4 + 16 + 24 + 16 + 12 + 12 + 16
 STEP_BYTES = 212.0
 
 
@@ -146,7 +151,7 @@ def build_context(N, replicas, precision, seed0=1000, stream=None):
     from paper_2103_10449_gb300 import inputs as I
     x, box = I.diamond(NCELL, NCELL, NCELL)
     sv = math.sqrt(KB * T_SW / (MASS * MVV2E))
-    ctx = N.Context(precision=precision, dt=0.001, skin=0.5, nbr_cap=48, stream=stream)
+    ctx = N.Context(precision=precision, dt=0.001, skin=SKIN, nbr_cap=48, stream=stream)
     for r in range(replicas):
         v = I.gaussian_velocities(len(x), sv, seed0 + r)
         s = ctx.add_system(x, box, v=v, r0=x, mass=MASS)
@@ -180,7 +185,7 @@ def free_energy_error(N, reps=8, n_eq=500, n_sw=2000):
     eq.close()
     out = {}
     for name, prec in (("fp64", N.NEFE_FP64), ("fp32", N.NEFE_FP32)):
-        c = N.Context(precision=prec, dt=0.001, skin=0.5, nbr_cap=48)
+        c = N.Context(precision=prec, dt=0.001, skin=SKIN, nbr_cap=48)
         for r in range(2 * reps):
             s = c.add_system(states[r][0], box, v=states[r][1], r0=x, mass=MASS)
             c.set_thermostat(s, T_SW, 0.1, 7000 + r)
@@ -199,6 +204,63 @@ def free_energy_error(N, reps=8, n_eq=500, n_sw=2000):
             "protocol": f"{reps} forward + {reps} backward FL realisations, {n_sw} steps each, 8000 atoms, 1000 K,"
                         f" identical initial states and noise seeds in both precisions",
             "systems_with_errors": out["fp64"][2] + out["fp32"][2]}
+
+
+def differentiation_throughput(N, torch):
+    """The differentiation workload: (i) the SW energy + forces + seven parameter derivatives
+    (nefe_sw_energy_grad, the backward of the autograd.Function) on diamond cells from 8000 to
+    1,000,000 atoms, atoms/s per precision; (ii) the checkpointed adjoint of the switching work
+    over 2000 steps of a 32768-atom liquid at 1700 K (K_c = 45), atom-steps/s of the forward
+    run and of the reverse sweep (which recomputes every segment)."""
+    from paper_2103_10449_gb300 import inputs as I
+    out = {"grad_sweep_atoms_per_s": {}}
+    prm = N.nefe_sw_params_silicon()
+    rcs = 1.80 * 2.0951 + 0.5
+    cap = 48
+    for nc in (10, 20, 32, 40, 50):
+        x, box = I.diamond(nc, nc, nc)
+        n = len(x)
+        xd = torch.tensor(np.ascontiguousarray(x.T).reshape(-1), dtype=torch.float64, device="cuda")
+        nbr = torch.empty(n * cap, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+        f = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+        eg = torch.empty(8, dtype=torch.float64, device="cuda")
+        N.nefe_neighbor_build(xd, n, box, rcs, cap, nbr, cnt)
+        row = {}
+        for name, prec in (("fp32", N.NEFE_FP32), ("fp64", N.NEFE_FP64)):
+            for _ in range(2):
+                N.nefe_sw_energy_grad(xd, n, box, rcs, nbr, cnt, cap, prm, prec, f, eg)
+            torch.cuda.synchronize()
+            reps = 5
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                N.nefe_sw_energy_grad(xd, n, box, rcs, nbr, cnt, cap, prm, prec, f, eg)
+            torch.cuda.synchronize()
+            row[name] = n * reps / (time.perf_counter() - t0)
+        out["grad_sweep_atoms_per_s"][str(n)] = row
+        del xd, nbr, cnt, f
+    x, box = I.liquid(32768, 0.05425, seed=51)
+    v = I.gaussian_velocities(len(x), math.sqrt(KB * 1700.0 / (MASS * MVV2E)), 52)
+    ctx = N.Context(precision=N.NEFE_FP32)
+    s = ctx.add_system(x, box, v=v)
+    ctx.set_thermostat(s, 1700.0, 0.1, 53)
+    ctx.run(1000)
+    x0, v0, _ = ctx.get_state(s)
+    ctx.close()
+    adj = N.Adjoint(x0, v0, box, kind=N.NEFE_SCHED_RS, lambda_f=0.5, T=1700.0, tdamp=0.1, seed=54, nsched=2000,
+                    checkpoint_every=45)
+    K = 2000
+    t0 = time.perf_counter()
+    adj.forward(K)
+    t1 = time.perf_counter()
+    g = adj.backward()
+    t2 = time.perf_counter()
+    adj.close()
+    out["adjoint"] = {"workload": "32768-atom liquid Si, 1700 K, reversible scaling 1 -> 0.5, 2000 steps, K_c = 45, FP64",
+                      "forward_atom_steps_per_s": len(x0) * K / (t1 - t0),
+                      "backward_atom_steps_per_s": len(x0) * K / (t2 - t1),
+                      "dW_dtheta": [float(v) for v in g]}
+    return out
 
 
 def time_steps(torch, ctx, stream, steps, md_steps):
@@ -327,11 +389,13 @@ def main():
     value = SH.aggregate_throughput([atoms * MD_STEPS * args.steps] * world, wall)
 
     # roofline of the dominant kernel (the longer force pass), from live CUDA-event durations
-    bytes_a = PASS_A_FIXED + 4.0 * mean_cnt
+    m_shell, _ = ctx.shell_stats()
+    bytes_a = PASS_A_FIXED + 4.0 * mean_cnt + 20.0 * m_shell
+    bytes_b = PASS_B_FIXED + 20.0 * m_shell
     if b_us > a_us:
-        kkey, kname, kbytes, kus = "k_gather", "k_gather (force pass B: neighbour-centred triplets, springs, Langevin, kick)", PASS_B_BYTES, b_us
+        kkey, kname, kbytes, kus = "k_gather", "k_gather (force pass B: leg forces of the neighbours' triplets, springs, Langevin, kick)", bytes_b, b_us
     else:
-        kkey, kname, kbytes, kus = "k_edges1", "k_edges1 (force pass A: shell, pair terms, triplets centred on the atom)", bytes_a, a_us
+        kkey, kname, kbytes, kus = "k_edges", "k_edges (force pass A: shell, pair terms, leg forces of the triplets centred on the atom)", bytes_a, a_us
     achieved = kbytes * atoms / (kus * 1e-6) / 1e9
     peak, peak_kind = peaks()
     tr = recorded_traffic(kkey)
@@ -348,7 +412,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": workload_config(R), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
-            "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild},
+            "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild, "mean_shell": m_shell},
             "systems_with_errors": errors}
     del ctx
 
@@ -392,6 +456,7 @@ def main():
         comp["batched_fp32_over_fp64_batched"] = value / world / comp["fp64_batched"]
         line["comparators"] = comp
         line["dG_err"] = free_energy_error(N)
+        line["differentiation"] = differentiation_throughput(N, torch)
         cps, nst, dt = cpu_baseline_sample()
         line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{nst} FP64-oracle MD steps of one 8000-atom replica ({dt:.1f} s)"}

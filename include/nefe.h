@@ -332,13 +332,15 @@ NEFE_API int nefe_load(nefe_ctx* ctx, const char* path);
 
 /* Times the variants of both force passes on the current state and keeps the fastest:
  * pass A with 1 (one thread per atom), 4, 8, 16 or 32 lanes per atom (FP64: 8, 16, 32),
- * pass B with 1 or 4 lanes per atom.  nefe_get_tuning reports pass A's lanes and the summed
+ * pass B with 1, 2, 4 or 8 lanes per atom (the list build keeps its lanes, 8 unless set).  nefe_get_tuning reports pass A's lanes and the summed
  * time of the two chosen passes; nefe_set_tuning fixes pass A's lanes. */
 NEFE_API int nefe_autotune(nefe_ctx* ctx);
 NEFE_API int nefe_get_tuning(nefe_ctx* ctx, int* lanes_per_atom, double* best_us);
 NEFE_API int nefe_set_tuning(nefe_ctx* ctx, int lanes_per_atom);
-/* Fixes pass B's lanes per atom (1 or 4). */
+/* Fixes pass B's lanes per atom (1, 2, 4 or 8). */
 NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
+/* Fixes the list build's lanes per atom (8, 16 or 32). */
+NEFE_API int nefe_set_list_tuning(nefe_ctx* ctx, int lanes_per_atom);
 
 /* Batched state transfer for every system at once: host (Ntot, 3) arrays, systems in the
  * order they were added (Ntot = sum of their n).  One host<->device copy each, the layout
@@ -353,6 +355,10 @@ NEFE_API int nefe_get_results_all(nefe_ctx* ctx, nefe_results* out, int count);
  * row length and the number of list builds so far (the initial build included). */
 NEFE_API int nefe_get_list_stats(nefe_ctx* ctx, int sys, double* mean_count, int* max_count,
                                  long* builds);
+
+/* In-cutoff shell statistics of the SW systems after the last force evaluation: mean and maximum
+ * number of neighbours inside the active cutoff per atom.  Blocking. */
+NEFE_API int nefe_get_shell_stats(nefe_ctx* ctx, double* mean_count, int* max_count);
 
 /* Kernel timing: with profiling enabled, the captured step graph records CUDA events around
  * the two force passes of every step; nefe_get_profile writes the mean time per step (us)

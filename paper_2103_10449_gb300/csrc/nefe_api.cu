@@ -73,6 +73,7 @@ int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap,
     NEFE_CU(S.alloc(&S.xs, v4 * (size_t)n));
     if (cells) {
         NEFE_CU(S.alloc(&S.xa, v4 * (size_t)n));
+        NEFE_CU(S.alloc(&S.xcs, v4 * (size_t)n));
         NEFE_CU(S.alloc(&S.q, sizeof(int4) * (size_t)n));
         NEFE_CU(S.alloc(&S.cell_of, sizeof(int) * (size_t)n));
         NEFE_CU(S.alloc(&S.perm, sizeof(int) * (size_t)n));
@@ -89,7 +90,7 @@ Bufs bufs_of(const Scratch1& S, const double* x, int n) {
     std::memset(&b, 0, sizeof(b));
     b.sys = S.sys; b.st = S.st; b.acc = S.acc; b.tile_sys = S.tile_sys;
     b.x = const_cast<double*>(x);
-    b.xs = S.xs; b.xa = S.xa; b.q = S.q; b.cell_of = S.cell_of; b.perm = S.perm;
+    b.xs = S.xs; b.xa = S.xa; b.xcs = S.xcs; b.q = S.q; b.cell_of = S.cell_of; b.perm = S.perm;
     b.shd = S.shd; b.shj = S.shj; b.shn = S.shn; b.P = S.P;
     b.cell_start = S.cell_start; b.cell_count = S.cell_count; b.cell_cursor = S.cell_cursor;
     b.ntot = n; b.swc = S.swc;
@@ -200,7 +201,7 @@ int nefe_sw_forces(const double* x, int n, const double box[3], double rcs, cons
         NEFE_CU(S.alloc(&S.shd, v4 * (size_t)n * kShell));
         NEFE_CU(S.alloc(&S.shj, sizeof(int) * (size_t)n * kShell));
         NEFE_CU(S.alloc(&S.shn, sizeof(int) * (size_t)n));
-        NEFE_CU(S.alloc(&S.P, v4 * (size_t)n));
+        NEFE_CU(S.alloc(&S.P, 3 * v4 * (size_t)n));
         Bufs b = bufs_of(S, x, n);
         b.nbr = const_cast<int*>(nbr); b.cnt = const_cast<int*>(cnt); b.cap = cap;
         b.f_out = f; b.e_atom = e_atom;
@@ -254,7 +255,7 @@ int nefe_sw_energy_grad(const double* x, int n, const double box[3], double rcs,
         NEFE_CU(S.alloc(&S.shd, v4 * (size_t)n * kShell));
         NEFE_CU(S.alloc(&S.shj, sizeof(int) * (size_t)n * kShell));
         NEFE_CU(S.alloc(&S.shn, sizeof(int) * (size_t)n));
-        NEFE_CU(S.alloc(&S.P, v4 * (size_t)n));
+        NEFE_CU(S.alloc(&S.P, 3 * v4 * (size_t)n));
         Bufs b = bufs_of(S, x, n);
         b.nbr = const_cast<int*>(nbr); b.cnt = const_cast<int*>(cnt); b.cap = cap;
         b.f_out = fo; b.e_atom = nullptr; b.want_grad = 1;

@@ -68,7 +68,7 @@ struct nefe_ctx {
     int* d_tile_sys = nullptr;
     double *d_x = nullptr, *d_r0 = nullptr, *d_ftmp = nullptr, *d_vtmp = nullptr;
     void *d_v = nullptr, *d_dhi = nullptr, *d_dlo = nullptr;
-    void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
+    void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_xcs = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
     void *d_shd = nullptr, *d_P = nullptr;
     int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr;
     int4* d_q = nullptr;
@@ -79,8 +79,9 @@ struct nefe_ctx {
     DevGroup* d_groups = nullptr;
     double* d_trace = nullptr;
     std::vector<void*> allocs;
-    int lanes = 8;           // pass A lanes per atom (1 = one thread per atom)
-    int glanes = 4;          // pass B lanes per atom
+    int lanes = 8;           // pass A lanes per atom (1 = one thread per atom, 4, 8, 16, 32)
+    int glanes = 4;          // pass B lanes per atom (1, 2, 4, 8)
+    int llanes = 8;          // list-build lanes per atom (8, 16, 32)
     double tune_us = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -96,7 +97,9 @@ struct nefe_ctx {
 
 namespace {
 
-int launches_per_step(const nefe_ctx* c) { return 8 + 2 * (int)c->chunk_tile0.size(); }
+// Per MD step: group update, kick/drift, rebuild worklist, cell count, scan, fill, list build,
+// and the two force passes per chunk.
+int launches_per_step(const nefe_ctx* c) { return 7 + 2 * (int)c->chunk_tile0.size(); }
 
 // Groups whole systems into chunks of at most `atoms` atoms (a larger system is a chunk of
 // its own).
@@ -357,12 +360,13 @@ int setup(nefe_ctx* c) {
     if ((rc = dalloc(c, &c->d_F, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_xs, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_xa, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_xcs, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_sd0, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_xi, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_shd, v4 * N * (size_t)kShell))) return rc;
     if ((rc = dalloc(c, &c->d_shj, sizeof(int) * N * (size_t)kShell))) return rc;
     if ((rc = dalloc(c, &c->d_shn, sizeof(int) * N))) return rc;
-    if ((rc = dalloc(c, &c->d_P, v4 * N))) return rc;
+    if ((rc = dalloc(c, &c->d_P, 3 * v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_rtiles, sizeof(int) * tile_sys.size()))) return rc;
     if ((rc = dalloc(c, &c->d_rcount, sizeof(int)))) return rc;
     if ((rc = dalloc(c, &c->d_q, sizeof(int4) * N))) return rc;
@@ -419,13 +423,14 @@ int setup(nefe_ctx* c) {
     std::memset(&b, 0, sizeof(b));
     b.sys = c->d_sys; b.st = c->d_st; b.acc = c->d_acc; b.tile_sys = c->d_tile_sys;
     b.x = c->d_x; b.v = c->d_v; b.dhi = c->d_dhi; b.dlo = c->d_dlo; b.r0 = c->d_r0; b.F = c->d_F;
-    b.xs = c->d_xs; b.xa = c->d_xa; b.sd0 = c->d_sd0; b.xi = c->d_xi;
+    b.xs = c->d_xs; b.xa = c->d_xa; b.xcs = c->d_xcs; b.sd0 = c->d_sd0; b.xi = c->d_xi;
     b.shd = c->d_shd; b.shj = c->d_shj; b.shn = c->d_shn; b.P = c->d_P;
     b.rtiles = c->d_rtiles; b.rcount = c->d_rcount;
     b.q = c->d_q; b.cell_of = c->d_cell_of; b.perm = c->d_perm; b.cell_start = c->d_cell_start;
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;
     b.trace = c->d_trace;
+    b.list_lanes = c->llanes;
 
     launch_inject(b, c->prec, c->ntiles, nullptr, c->d_vtmp, c->stream);
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * nsys * ACC_N * kSlots, c->stream));
@@ -878,10 +883,29 @@ int nefe_autotune(nefe_ctx* c) {
     launch_edges(b, c->prec, best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
     double best_g = 1e30;
     int best_gl = c->glanes;
-    for (int l : {1, 4}) {
-        const double us = time_us([&] { launch_gather(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches); });
-        if (us < best_g) { best_g = us; best_gl = l; }
+    {
+        // pass B is timed in its step form (springs, Langevin, kick) on scratch copies of the
+        // velocities and the force, so the state is left as it was
+        const size_t el = c->prec == NEFE_FP64 ? sizeof(double) : sizeof(float);
+        const size_t v4 = 4 * el;
+        void *tv = nullptr, *tf = nullptr;
+        NEFE_CU(cudaMalloc(&tv, el * 3 * c->ntot));
+        NEFE_CU(cudaMalloc(&tf, v4 * c->ntot));
+        NEFE_CU(cudaMemcpyAsync(tv, c->d_v, el * 3 * c->ntot, cudaMemcpyDeviceToDevice, c->stream));
+        Bufs bs = b;
+        bs.v = tv;
+        bs.F = tf;
+        for (int l : {1, 2, 4, 8}) {
+            const double us = time_us([&] { launch_gather(bs, c->prec, l, c->ntiles, FM_STEP, c->stream, &c->launches); });
+            if (us < best_g) { best_g = us; best_gl = l; }
+        }
+        NEFE_CU(cudaStreamSynchronize(c->stream));
+        cudaFree(tv);
+        cudaFree(tf);
     }
+    // the list build keeps its lanes: a full rebuild (the only thing timeable here) ranks the
+    // variants differently from the partial rebuilds of a run, where 8 lanes were measured best
+    const int best_ll = c->llanes;
     // chunking of the two passes (L2 residency of the shells against parallelism per launch)
     const int old_chunk = c->chunk_atoms;
     double best_c = 1e30;
@@ -902,9 +926,11 @@ int nefe_autotune(nefe_ctx* c) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     NEFE_CU(cudaGetLastError());
-    if (best_l != c->lanes || best_gl != c->glanes || best_ca != old_chunk) drop_graph(c);
+    if (best_l != c->lanes || best_gl != c->glanes || best_ll != c->llanes || best_ca != old_chunk) drop_graph(c);
     c->lanes = best_l;
     c->glanes = best_gl;
+    c->llanes = best_ll;
+    c->b.list_lanes = best_ll;
     c->tune_us = best_c;
     return NEFE_OK;
 }
@@ -975,6 +1001,33 @@ int nefe_get_results_all(nefe_ctx* c, nefe_results* out, int count) {
     }
     NEFE_CU(cudaStreamSynchronize(c->stream));
     for (int s = 0; s < count; ++s) fill_results(S[s], st[s], out + s);
+    return NEFE_OK;
+}
+
+int nefe_get_shell_stats(nefe_ctx* c, double* mean_count, int* max_count) {
+    if (!c) return fail(NEFE_EINVAL, "context is NULL");
+    int rc = setup(c);
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    std::vector<int> shn(c->ntot);
+    std::vector<DevSys> S(c->nsys);
+    NEFE_CU(cudaMemcpyAsync(shn.data(), c->d_shn, sizeof(int) * c->ntot, cudaMemcpyDeviceToHost, c->stream));
+    NEFE_CU(cudaMemcpyAsync(S.data(), c->d_sys, sizeof(DevSys) * c->nsys, cudaMemcpyDeviceToHost, c->stream));
+    NEFE_CU(cudaStreamSynchronize(c->stream));
+    double sum = 0.0;
+    long long n = 0;
+    int mx = 0;
+    for (int s = 0; s < c->nsys; ++s) {
+        if (S[s].pot != POT_SW) continue;
+        for (int i = 0; i < S[s].n; ++i) {
+            const int v = shn[S[s].off + i];
+            sum += v;
+            mx = std::max(mx, v);
+        }
+        n += S[s].n;
+    }
+    if (mean_count) *mean_count = n > 0 ? sum / (double)n : 0.0;
+    if (max_count) *max_count = mx;
     return NEFE_OK;
 }
 
@@ -1061,9 +1114,20 @@ int nefe_get_profile(nefe_ctx* c, double* us, long* samples) {
 
 int nefe_set_gather_tuning(nefe_ctx* c, int lanes) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
-    if (lanes != 1 && lanes != 4) return fail(NEFE_EINVAL, "pass B supports 1 or 4 lanes per atom");
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+        return fail(NEFE_EINVAL, "pass B supports 1, 2, 4 or 8 lanes per atom");
     if (lanes != c->glanes) drop_graph(c);
     c->glanes = lanes;
+    return NEFE_OK;
+}
+
+int nefe_set_list_tuning(nefe_ctx* c, int lanes) {
+    if (!c) return fail(NEFE_EINVAL, "context is NULL");
+    if (lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(NEFE_EINVAL, "the list build supports 8, 16 or 32 lanes per atom");
+    if (lanes != c->llanes) drop_graph(c);
+    c->llanes = lanes;
+    c->b.list_lanes = lanes;
     return NEFE_OK;
 }
 

@@ -76,6 +76,7 @@ struct Scratch1 {
     int4* q = nullptr;
     void* xs = nullptr;
     void* xa = nullptr;
+    void* xcs = nullptr;
     void* shd = nullptr;
     int* shj = nullptr;
     int* shn = nullptr;

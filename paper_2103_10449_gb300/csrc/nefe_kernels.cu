@@ -9,13 +9,14 @@
 //                 affine box drift), kept as a compensated pair in the FP32 path; mirror
 //                 xs = x - q h; displacement test -> rebuild flag; thermostat noise + its sum.
 //   rebuild       (flagged systems) fold the displacement into the FP64 anchor, cell count ->
-//                 scan -> fill -> per-cell sort -> Verlet list.
-//   k_edges       force pass A: in-cutoff shell of each atom (stored compactly), pair terms,
-//                 the triplets centred on the atom (force on it, energy, virial).
-//   k_gather      force pass B: the atom's pass-A force plus, from the stored shells, the
-//                 force of every triplet centred on a neighbour in which the atom is a leg
-//                 (a gather: no atomics, bitwise reproducible); Einstein springs, lambda
-//                 mixing, Langevin force with its per-system mean removed, second half kick.
+//                 scan -> fill (with a cell-ordered copy of the mirror) -> Verlet list.
+//   k_edges       force pass A: in-cutoff shell of each atom, pair terms, and for each shell
+//                 edge the force its triplets exert on the leg atom (stored per edge); the
+//                 atom's own force, energy and virial.
+//   k_gather      force pass B: the atom's pass-A force plus the leg forces that the triplets
+//                 centred on its neighbours exert on it (a gather: no atomics, bitwise
+//                 reproducible); Einstein springs, lambda mixing, Langevin force with its
+//                 per-system mean removed, second half kick.
 //
 // Positions: the FP64 anchor x (positions at the last list build) plus the displacement
 // since then (FP64, or an FP32 value + FP32 compensation term, ~2^-48 relative).  The anchor
@@ -218,16 +219,23 @@ __device__ void cells_count_tile(const Bufs& b, int tile) {
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
-    int n3[3];
-    const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, n3);
-    double h[3];
-    for (int k = 0; k < 3; ++k) h[k] = __ddiv_rn(st.box[k], (double)n3[k]);
-    if (tile == S.tile0 && threadIdx.x == 0) {
-        for (int k = 0; k < 3; ++k) { st.ncell[k] = n3[k]; st.h[k] = h[k]; st.hb[k] = h[k]; }
-        refresh_box_f(st);
-        st.nbuild += 1;
-        if (!ok) atomicOr(&st.err, NEFE_ERR_BOX);
+    __shared__ int s_n3[3];
+    __shared__ double s_h[3];
+    if (threadIdx.x == 0) {                      // the grid of this tile's system, once per tile
+        int g3[3];
+        const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, g3);
+        for (int k = 0; k < 3; ++k) { s_n3[k] = g3[k]; s_h[k] = __ddiv_rn(st.box[k], (double)g3[k]); }
+        if (tile == S.tile0) {
+            for (int k = 0; k < 3; ++k) { st.ncell[k] = g3[k]; st.h[k] = s_h[k]; st.hb[k] = s_h[k]; }
+            refresh_box_f(st);
+            st.nbuild += 1;
+            if (!ok) atomicOr(&st.err, NEFE_ERR_BOX);
+        }
     }
+    __syncthreads();
+    const int n3[3] = {s_n3[0], s_n3[1], s_n3[2]};
+    const double h[3] = {s_h[0], s_h[1], s_h[2]};
+    __syncthreads();                             // the next tile of the loop rewrites the table
     if ((int)threadIdx.x >= ta.count) return;
     const int i = ta.first + threadIdx.x;
     const size_t N = b.ntot;
@@ -351,8 +359,18 @@ __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
     }
 }
 
-// R3: scatter atoms into their cell segment (order inside a cell fixed by R4).
+// Atom index carried in the .w lane of a position vector (bit pattern in FP32, value in FP64).
+template <typename T> __device__ __forceinline__ T pack_index(int i);
+template <> __device__ __forceinline__ float pack_index<float>(int i) { return __int_as_float(i); }
+template <> __device__ __forceinline__ double pack_index<double>(int i) { return (double)i; }
+__device__ __forceinline__ int unpack_index(float w) { return __float_as_int(w); }
+__device__ __forceinline__ int unpack_index(double w) { return (int)w; }
+
+// R3: scatter atoms into their cell segment (order inside a cell fixed by R4), with a copy
+// of their mirror positions in the same order for the list build.
+template <typename T>
 __device__ void cells_fill_tile(const Bufs& b, int tile) {
+    using T4 = typename V4<T>::t;
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     if ((int)threadIdx.x >= ta.count) return;
@@ -363,9 +381,14 @@ __device__ void cells_fill_tile(const Bufs& b, int tile) {
         return;
     }
     b.perm[S.off + pos] = i;
+    if (b.xcs) {
+        const T4 m = reinterpret_cast<const T4*>(b.xs)[i];
+        reinterpret_cast<T4*>(b.xcs)[S.off + pos] = mk4(m.x, m.y, m.z, pack_index<T>(i));
+    }
 }
+template <typename T>
 __global__ void __launch_bounds__(kTile) k_cells_fill(Bufs b) {
-    NEFE_FOR_TILES(b, cells_fill_tile(b, tile));
+    NEFE_FOR_TILES(b, cells_fill_tile<T>(b, tile));
 }
 
 // R4: insertion sort of each cell segment by atom index (stable order by (cell, atom)).
@@ -390,8 +413,8 @@ __global__ void __launch_bounds__(256) k_cells_sort(Bufs b, int force_all) {
 
 // Exact list criterion in FP64, the plain definition: raw = x_j - x_i, m = rint(raw/L),
 // d = raw - m L, ((d_x^2 + d_y^2) + d_z^2) < rcs^2; every operation rounded separately.
-__device__ __forceinline__ bool exact_pair_in(const Bufs& b, const double box[3], int i, int j,
-                                              double rcs2, double d[3]) {
+__device__ __noinline__ bool exact_pair_in(const Bufs& b, const double box[3], int i, int j,
+                                           double rcs2, double d[3]) {
     for (int k = 0; k < 3; ++k) {
         const double raw = __dsub_rn(b.x[(size_t)k * b.ntot + j], b.x[(size_t)k * b.ntot + i]);
         const double m = rint(__ddiv_rn(raw, box[k]));
@@ -408,19 +431,18 @@ __device__ __forceinline__ bool exact_pair_in(const Bufs& b, const double box[3]
 // 1e-10 (FP64) around rcs^2, and inside the band by the exact FP64 criterion (which must
 // also agree with the offset's image), so the list equals the plain definition bit for
 // bit.  Accepted entries are ranked by atom index (a rank count, no atomics) into the row.
-constexpr int kListLanes = 8;
 constexpr int kRebuildBlocks = 152 * 8;   // bounded grid of the worklist-driven rebuild kernels
-template <typename T>
-__device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap], int (*cstart)[28],
-                           int (*ccell)[27]) {
+template <typename T, int L>
+__device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap + 1], int (*cstart)[28],
+                           int (*cbase)[27]) {
     using T4 = typename V4<T>::t;
-    constexpr int L = kListLanes, G = kTile / L;
+    constexpr int G = kTile / L;
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
-    const unsigned gmask = ((1u << L) - 1u) << lbase;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
     const int ia = part * G + grp;
     const bool valid = ia < ta.count;
     const int i = ta.first + ia;
@@ -437,13 +459,14 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
         zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
         const int c2 = xx + nx * (yy + ny * zz);
         const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
-        ccell[grp][o] = c2;
+        cbase[grp][o] = lo;
         cstart[grp][o + 1] = hi - lo;
     }
     __syncwarp(gmask);
     if (lane == 0) {
         cstart[grp][0] = 0;
         for (int o = 1; o <= 27; ++o) cstart[grp][o] += cstart[grp][o - 1];
+        for (int o = 0; o < 27; ++o) cbase[grp][o] -= cstart[grp][o];   // p = cbase[o] + f
     }
     __syncwarp(gmask);
     const int total = cstart[grp][27];
@@ -458,43 +481,59 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
         hi2 = S.rcs * S.rcs * (1.0 + 1e-10);
     }
     const int cap = b.cap;
+    // candidates in cell order: consecutive candidates of a cell are consecutive in xcs
+    const T4* xc = reinterpret_cast<const T4*>(b.xcs) + S.off;
     int count = 0;
     int o = 0;
-    for (int base = 0; base < total; base += L) {
-        const int f = base + lane;
-        bool in = false;
-        int e = 0;
-        if (f < total) {
-            while (f >= cstart[grp][o + 1]) ++o;
-            const int c2 = ccell[grp][o];
-            const int j = b.perm[S.off + max(0, min(start[c2], S.n)) + (f - cstart[grp][o])];
-            const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-            if (j < S.off || j >= S.off + S.n) {
-                atomicOr(&st.err, NEFE_ERR_CELL);
-            } else if (!(j == i && o == 13)) {
-                const T4 xj = reinterpret_cast<const T4*>(b.xs)[j];
-                const T dx = xj.x - xi.x + (T)ox * hx;
-                const T dy = xj.y - xi.y + (T)oy * hy;
-                const T dz = xj.z - xi.z + (T)oz * hz;
-                const T dd = dx * dx + dy * dy + dz * dz;
-                if (dd < lo2) {
-                    in = true;
-                } else if (dd <= hi2) {
-                    double d[3];
-                    in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
-                    in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
-                         fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
-                         fabs(d[2] - (double)dz) < 0.5 * st.h[2];
-                }
-                e = j | (o << kCodeShift);
+    constexpr int NB = 2;
+    for (int base = 0; base < total; base += NB * L) {
+        T4 xj[NB];
+        int oo[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int f = base + u * L + lane;
+            oo[u] = -1;
+            if (f < total) {
+                while (f >= cstart[grp][o + 1]) ++o;
+                oo[u] = o;
+                const int p = cbase[grp][o] + f;
+                xj[u] = xc[p < 0 ? 0 : (p >= S.n ? S.n - 1 : p)];
             }
         }
-        const unsigned bal = __ballot_sync(gmask, in);
-        if (in) {
-            const int pos = count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
-            if (pos < kMaxCap) buf[grp][pos] = e;
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            bool in = false;
+            int e = 0;
+            const int ou = oo[u];
+            if (ou >= 0) {
+                const int j = unpack_index(xj[u].w);
+                const int ox = ou % 3 - 1, oy = (ou / 3) % 3 - 1, oz = ou / 9 - 1;
+                if (j < S.off || j >= S.off + S.n) {
+                    atomicOr(&st.err, NEFE_ERR_CELL);
+                } else if (!(j == i && ou == 13)) {
+                    const T dx = xj[u].x - xi.x + (T)ox * hx;
+                    const T dy = xj[u].y - xi.y + (T)oy * hy;
+                    const T dz = xj[u].z - xi.z + (T)oz * hz;
+                    const T dd = dx * dx + dy * dy + dz * dz;
+                    if (dd < lo2) {
+                        in = true;
+                    } else if (dd <= hi2) {
+                        double d[3];
+                        in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
+                        in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
+                             fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
+                             fabs(d[2] - (double)dz) < 0.5 * st.h[2];
+                    }
+                    e = j | (ou << kCodeShift);
+                }
+            }
+            const unsigned bal = __ballot_sync(gmask, in);
+            if (in) {
+                const int pos = count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+                if (pos < kMaxCap) buf[grp][pos] = e;
+            }
+            count += __popc(bal);
         }
-        count += __popc(bal);
     }
     __syncwarp(gmask);
     // rank by atom index into the row (indices in a row are distinct)
@@ -515,18 +554,18 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     __syncwarp(gmask);                           // shared tables reused by the next item
 }
 
-template <typename T>
+template <typename T, int L>
 __global__ void __launch_bounds__(kTile) k_nlist(Bufs b) {
-    constexpr int L = kListLanes, G = kTile / L;
-    __shared__ int buf[G][kMaxCap];
+    constexpr int G = kTile / L;
+    __shared__ int buf[G][kMaxCap + 1];   // padded: the groups of a warp on different banks
     __shared__ int cstart[G][28];
-    __shared__ int ccell[G][27];
+    __shared__ int cbase[G][27];
     if (b.rtiles) {
         const int n = *b.rcount * L;
         for (int w = blockIdx.x; w < n; w += gridDim.x)
-            nlist_item<T>(b, b.rtiles[w / L], w % L, buf, cstart, ccell);
+            nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cstart, cbase);
     } else {
-        nlist_item<T>(b, blockIdx.x / L, blockIdx.x % L, buf, cstart, ccell);
+        nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, buf, cstart, cbase);
     }
 }
 
@@ -703,19 +742,29 @@ __device__ __forceinline__ void sw_pair_pgrad(const SWc<T>& P, T r, T out[5]) {
     out[4] = phi * id * id;             // d/da (pair exponent)
 }
 
-// Force pass A.  L lanes per atom, 128/L atoms per block, the in-cutoff shell staged in
-// shared memory and also stored compactly (d_ij and g_ij per entry, neighbour index) for
-// pass B.  Pair terms on the lanes that find the edge; triplets (i; a, b), a < b, dealt
-// over the lanes.  Writes the atom's force from these terms (P.xyz) and its energy (P.w:
-// half of each pair term, every triplet centred on it); block sums of energy and virial.
+// Force pass A.  L lanes per atom, 128/L atoms per block.
+//  1. The lanes compact the atom's Verlet row into its in-cutoff shell: (d, r^2) in shared
+//     memory, the neighbour indices in shj (ended by -1 when shorter than kShell).
+//  2. Lane a owns shell edge a: pair term (full force on i, half the energy), g, dg/dr and the
+//     unit vector u_a.
+//  3. Lane a sums over the other edges b the force that triplet (i; a, b) exerts on the leg
+//     atom j_a,  F_a(b) = -t1 u_b + (t1 c - t2) u_a  with  c = u_a.u_b,
+//     t1 = 2 eps lambda (c - c0) g_a g_b / r_a,  t2 = eps lambda (c - c0)^2 g_b (dg/dr)_a,
+//     and stores the leg force L_a = sum_b F_a(b) in shd[i][a] for pass B.  Atom i gets -L_a
+//     (the three forces of a triplet sum to zero) and half of h(i; a, b) per ordered pair.
+// Each ordered pair costs ~14 flops and every triplet force is computed exactly once.
+// P[i] = (pair + own triplet force, atom energy); block sums of energy and virial (and, with
+// want_grad, of dE/d(A, B, p, q, a, lambda3, gamma)).
 template <typename T, int L>
 __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int G = kTile / L;
-    __shared__ T4 sh_d[G][kShell];
-    __shared__ T sh_g[G][kShell];
-    __shared__ T sh_dg[G][kShell];
-    __shared__ T sh_id[G][kShell];
+    // rows padded by one entry: the groups of a warp then start on different banks
+    __shared__ T4 sh_u[G][kShell + 1];     // (d, r^2) after compaction, then (u, r)
+    __shared__ T sh_g[G][kShell + 1];
+    __shared__ T sh_dg[G][kShell + 1];
+    __shared__ T sh_id[G][kShell + 1];     // 1/(s - a), parameter gradients only
+    __shared__ T4 soff[27];
 
     const int tile = blockIdx.x / L + b.tile_base, part = blockIdx.x % L;
     const TileAtom ta = tile_of(b, tile);
@@ -726,7 +775,6 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
-    __shared__ T4 soff[27];
     offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
     const int ia = part * G + grp;
     const bool valid = ia < ta.count;
@@ -740,241 +788,259 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
         const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
         const int ci = min(b.cnt[i], b.cap);
         const int* row = b.nbr + (size_t)i * b.cap;
-        T4* Sd = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
+        T4* Fl = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
         int* Sj = b.shj + (size_t)i * kShell;
+        // 1. compaction, NB row entries per lane in flight (row loads, then position gathers)
+        constexpr int NB = (24 + L - 1) / L;
         int m = 0;
-        for (int base = 0; base < ci; base += L) {
-            const int sidx = base + lane;
-            bool in = false;
-            T dx = 0, dy = 0, dz = 0, r2 = 0;
-            int j = 0;
-            if (sidx < ci) {
-                const int e = row[sidx];
-                j = e & (int)kIndexMask;
-                const T4 oh = soff[(unsigned)e >> kCodeShift];
-                const T4 xj = reinterpret_cast<const T4*>(b.xs)[j];
-                dx = (xj.x - xi.x) + oh.x;
-                dy = (xj.y - xi.y) + oh.y;
-                dz = (xj.z - xi.z) + oh.z;
-                r2 = dx * dx + dy * dy + dz * dz;
-                in = r2 < P.act2;
+        for (int base = 0; base < ci; base += NB * L) {
+            int e[NB];
+            T4 xj[NB];
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int sidx = base + u * L + lane;
+                e[u] = sidx < ci ? row[sidx] : 0;
             }
-            const unsigned bal = __ballot_sync(gmask, in);
-            if (in) {
-                const int pos = m + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
-                if (pos < kShell) {
-                    const T r = r2 * xrsqrt(r2);
-                    T phi, dphi, g, dg;
-                    sw_edge<T>(P, r, phi, dphi, g, dg);
-                    sh_d[grp][pos] = mk4(dx, dy, dz, r);
-                    sh_g[grp][pos] = g;
-                    sh_dg[grp][pos] = dg;
-                    Sd[pos] = mk4(dx, dy, dz, g);
-                    Sj[pos] = j;
-                    if (grad) {   // each pair is seen from both ends: half of each derivative
-                        T pg[5];
-                        sw_pair_pgrad<T>(P, r, pg);
-                        for (int k = 0; k < 5; ++k) gth[k] += (T)0.5 * pg[k];
-                        const T den = r * P.inv_sig - P.a;
-                        sh_id[grp][pos] = den < -cut_eps<T>() ? xrcp(den) : (T)0;
-                    }
-                    const T c = dphi * xrcp(r);
-                    fx += c * dx; fy += c * dy; fz += c * dz;
-                    en += (T)0.5 * phi;
-                    const T hc = (T)-0.5 * c;
-                    w0 += hc * dx * dx; w1 += hc * dy * dy; w2 += hc * dz * dz;
-                    w3 += hc * dx * dy; w4 += hc * dx * dz; w5 += hc * dy * dz;
+#pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (base + u * L + lane < ci) xj[u] = reinterpret_cast<const T4*>(b.xs)[e[u] & (int)kIndexMask];
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int sidx = base + u * L + lane;
+                bool in = false;
+                T dx = 0, dy = 0, dz = 0, r2 = 0;
+                if (sidx < ci) {
+                    const T4 oh = soff[(unsigned)e[u] >> kCodeShift];
+                    dx = (xj[u].x - xi.x) + oh.x;
+                    dy = (xj[u].y - xi.y) + oh.y;
+                    dz = (xj[u].z - xi.z) + oh.z;
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    in = r2 < P.act2;
                 }
+                const unsigned bal = __ballot_sync(gmask, in);
+                if (in) {
+                    const int pos = m + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+                    if (pos < kShell) {
+                        sh_u[grp][pos] = mk4(dx, dy, dz, r2);
+                        Sj[pos] = e[u] & (int)kIndexMask;
+                    }
+                }
+                m += __popc(bal);
             }
-            m += __popc(bal);
         }
         if (m > kShell) {
             if (lane == 0) atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
             m = kShell;
         }
+        if (lane == 0 && m < kShell) Sj[m] = -1;
         __syncwarp(gmask);
-        // triplets centred at i: pairs (a < b) of the shell, flat index dealt mod L
-        int t0 = 0;
-        for (int a = 0; a < m - 1; ++a) {
-            const int rowlen = m - 1 - a;
-            const int off = (lane - t0) & (L - 1);
-            if (off < rowlen) {
-                const T4 da = sh_d[grp][a];
-                const T ga = sh_g[grp][a], dga = sh_dg[grp][a];
-                const T ira = xrcp(da.w);
-                const T uax = da.x * ira, uay = da.y * ira, uaz = da.z * ira;
-                for (int bb = a + 1 + off; bb < m; bb += L) {
-                    const T4 db = sh_d[grp][bb];
-                    const T gb = sh_g[grp][bb], dgb = sh_dg[grp][bb];
-                    const T irb = xrcp(db.w);
-                    const T ubx = db.x * irb, uby = db.y * irb, ubz = db.z * irb;
-                    const T c = uax * ubx + uay * uby + uaz * ubz;
-                    const T dc = c - P.c0;
-                    const T two = (T)2 * P.epslam * dc * ga * gb;
-                    const T dc2 = P.epslam * dc * dc;
-                    const T ta_ = two * ira, tb_ = two * irb;
-                    const T fax = -(ta_ * (ubx - c * uax) + dc2 * dga * gb * uax);
-                    const T fay = -(ta_ * (uby - c * uay) + dc2 * dga * gb * uay);
-                    const T faz = -(ta_ * (ubz - c * uaz) + dc2 * dga * gb * uaz);
-                    const T fbx = -(tb_ * (uax - c * ubx) + dc2 * ga * dgb * ubx);
-                    const T fby = -(tb_ * (uay - c * uby) + dc2 * ga * dgb * uby);
-                    const T fbz = -(tb_ * (uaz - c * ubz) + dc2 * ga * dgb * ubz);
-                    fx -= fax + fbx; fy -= fay + fby; fz -= faz + fbz;
-                    en += dc2 * ga * gb;
-                    if (grad) {
-                        const T hh = dc2 * ga * gb;
-                        const T ia_ = sh_id[grp][a], ib_ = sh_id[grp][bb];
-                        gth[4] += hh * P.gam * (ia_ * ia_ + ib_ * ib_);
-                        gth[5] += P.eps * dc * dc * ga * gb;
-                        gth[6] += hh * (ia_ + ib_);
-                    }
-                    w0 += da.x * fax + db.x * fbx;
-                    w1 += da.y * fay + db.y * fby;
-                    w2 += da.z * faz + db.z * fbz;
-                    w3 += (T)0.5 * (da.x * fay + da.y * fax + db.x * fby + db.y * fbx);
-                    w4 += (T)0.5 * (da.x * faz + da.z * fax + db.x * fbz + db.z * fbx);
-                    w5 += (T)0.5 * (da.y * faz + da.z * fay + db.y * fbz + db.z * fby);
+        // 2. edges: pair terms, g, dg, unit vectors
+        for (int a = lane; a < m; a += L) {
+            const T4 d = sh_u[grp][a];
+            const T ir = xrsqrt(d.w);
+            const T r = d.w * ir;
+            T phi, dphi, g, dg;
+            sw_edge<T>(P, r, phi, dphi, g, dg);
+            const T c = dphi * ir;
+            fx += c * d.x; fy += c * d.y; fz += c * d.z;
+            en += (T)0.5 * phi;
+            const T hc = (T)-0.5 * c;
+            w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
+            w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
+            sh_u[grp][a] = mk4(d.x * ir, d.y * ir, d.z * ir, r);
+            sh_g[grp][a] = g;
+            sh_dg[grp][a] = dg;
+            if (grad) {   // each pair is seen from both ends: half of each derivative
+                T pg[5];
+                sw_pair_pgrad<T>(P, r, pg);
+                for (int k = 0; k < 5; ++k) gth[k] += (T)0.5 * pg[k];
+                const T den = r * P.inv_sig - P.a;
+                sh_id[grp][a] = den < -cut_eps<T>() ? xrcp(den) : (T)0;
+            }
+        }
+        __syncwarp(gmask);
+        // 3. leg forces
+        for (int a = lane; a < m; a += L) {
+            const T4 ua = sh_u[grp][a];
+            const T ga = sh_g[grp][a];
+            const T k1 = (T)2 * P.epslam * ga * xrcp(ua.w);
+            const T k2 = P.epslam * sh_dg[grp][a];
+            T ax = 0, ay = 0, az = 0, cc = 0, eh = 0, e1 = 0, e2 = 0;
+            for (int bb = 0; bb < m; ++bb) {
+                if (bb == a) continue;
+                const T4 ub = sh_u[grp][bb];
+                const T gb = sh_g[grp][bb];
+                const T c = ua.x * ub.x + ua.y * ub.y + ua.z * ub.z;
+                const T dc = c - P.c0;
+                const T s1 = dc * gb;
+                const T t1 = k1 * s1;
+                ax += t1 * ub.x; ay += t1 * ub.y; az += t1 * ub.z;
+                cc += t1 * c - k2 * dc * s1;
+                const T hb = dc * s1;                    // (c - c0)^2 g_b
+                eh += hb;
+                if (grad) {
+                    const T idb = sh_id[grp][bb];
+                    e1 += hb * idb;
+                    e2 += hb * idb * idb;
                 }
             }
-            t0 += rowlen;
+            const T lx = cc * ua.x - ax, ly = cc * ua.y - ay, lz = cc * ua.z - az;
+            Fl[a] = mk4(lx, ly, lz, (T)0);
+            fx -= lx; fy -= ly; fz -= lz;
+            const T hsum = (T)0.5 * P.epslam * ga * eh;  // half of every triplet (i; a, b), b != a
+            en += hsum;
+            const T dx = ua.x * ua.w, dy = ua.y * ua.w, dz = ua.z * ua.w;
+            w0 += dx * lx; w1 += dy * ly; w2 += dz * lz;
+            w3 += (T)0.5 * (dx * ly + dy * lx);
+            w4 += (T)0.5 * (dx * lz + dz * lx);
+            w5 += (T)0.5 * (dy * lz + dz * ly);
+            if (grad) {
+                const T ida = sh_id[grp][a];
+                const T hh = (T)0.5 * P.epslam * ga;
+                gth[4] += hh * P.gam * (ida * ida * eh + e2);
+                gth[5] += (T)0.5 * P.eps * ga * eh;
+                gth[6] += hh * (ida * eh + e1);
+            }
         }
-        T e_own = en;
+        // the atom's force, energy and virial (summed over its lanes); pass B adds the energy
+        // and virial to its block sums, so this pass has no block reduction
+        T v[10] = {fx, fy, fz, en, w0, w1, w2, w3, w4, w5};
 #pragma unroll
-        for (int o = L / 2; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(gmask, fx, o);
-            fy += __shfl_xor_sync(gmask, fy, o);
-            fz += __shfl_xor_sync(gmask, fz, o);
-            e_own += __shfl_xor_sync(gmask, e_own, o);
-        }
+        for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 10; ++k) v[k] += __shfl_xor_sync(gmask, v[k], o);
         if (lane == 0) {
-            reinterpret_cast<T4*>(b.P)[i] = mk4(fx, fy, fz, e_own);
+            T4* Pa = reinterpret_cast<T4*>(b.P);
+            Pa[i] = mk4(v[0], v[1], v[2], v[3]);
+            Pa[b.ntot + 2 * (size_t)i] = mk4(v[4], v[5], v[6], v[7]);
+            Pa[b.ntot + 2 * (size_t)i + 1] = mk4(v[8], v[9], (T)0, (T)0);
             b.shn[i] = m;
         }
     }
-    T red[8] = {en, (T)0, w0, w1, w2, w3, w4, w5};
-    block_sum_to_acc<T, 8>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
     if (grad) block_sum_to_acc<T, 7>(gth, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_DTH, &st.err);
 }
 
-// Force pass A, one thread per atom (64-thread blocks, half a tile each).  The row is first
-// compacted into the thread's active shell (kShell1 entries in shared memory, one column
-// per thread), then edges (pair terms, g, dg) and the triplets centred on the atom are
-// evaluated by the same thread, so no lane idles while another holds an edge.
+// Force pass A, one thread per atom (64-thread blocks, half a tile each), FP32: the same
+// three phases as k_edges with the shell in shared memory, one column per thread (kShell1
+// entries), and no lane coordination (no ballots, no idle lanes while another holds edges).
 constexpr int kShell1 = 20;
 constexpr int kEdges1Threads = 64;
 template <typename T>
 __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
-    __shared__ T4 sh_d[kShell1][NT];
+    __shared__ T4 sh_u[kShell1][NT];     // (d, r^2) after compaction, then (u, r)
     __shared__ T sh_g[kShell1][NT];
     __shared__ T sh_dg[kShell1][NT];
+    __shared__ T4 soff[27];
     const int tile = blockIdx.x / (kTile / NT) + b.tile_base, part = blockIdx.x % (kTile / NT);
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
     if (S.pot != POT_SW) return;                 // uniform over the block
     const SWc<T> P = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
-    __shared__ T4 soff[27];
     offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
     const int t = threadIdx.x;
     const int ia = part * NT + t;
+    if (ia >= ta.count) return;
+    const int i = ta.first + ia;
+    const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
+    const int ci = min(b.cnt[i], b.cap);
+    const int* row = b.nbr + (size_t)i * b.cap;
+    T4* Fl = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
+    int* Sj = b.shj + (size_t)i * kShell;
+    // 1. compaction, four row entries in flight
+    int m = 0;
+    for (int base = 0; base < ci; base += 4) {
+        int e[4];
+        T4 xj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = (base + u < ci) ? row[base + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (base + u < ci) xj[u] = reinterpret_cast<const T4*>(b.xs)[e[u] & (int)kIndexMask];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (base + u >= ci) continue;
+            const T4 oh = soff[(unsigned)e[u] >> kCodeShift];
+            const T dx = (xj[u].x - xi.x) + oh.x, dy = (xj[u].y - xi.y) + oh.y, dz = (xj[u].z - xi.z) + oh.z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.act2) {
+                if (m < kShell1) {
+                    sh_u[m][t] = mk4(dx, dy, dz, r2);
+                    Sj[m] = e[u] & (int)kIndexMask;
+                }
+                ++m;
+            }
+        }
+    }
+    if (m > kShell1) {
+        atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
+        m = kShell1;
+    }
+    if (m < kShell) Sj[m] = -1;
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-    if (ia < ta.count) {
-        const int i = ta.first + ia;
-        const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
-        const int ci = min(b.cnt[i], b.cap);
-        const int* row = b.nbr + (size_t)i * b.cap;
-        T4* Sd = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
-        int* Sj = b.shj + (size_t)i * kShell;
-        int m = 0;
-        for (int base = 0; base < ci; base += 4) {       // compaction: distance test only,
-            int e[4];                                     // four candidates in flight (entries
-            T4 xj[4];                                     // with code >= 16 are negative ints)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = (base + u < ci) ? row[base + u] : 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (base + u < ci) xj[u] = reinterpret_cast<const T4*>(b.xs)[e[u] & (int)kIndexMask];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (base + u >= ci) continue;
-                const T4 oh = soff[(unsigned)e[u] >> kCodeShift];
-                const T dx = (xj[u].x - xi.x) + oh.x, dy = (xj[u].y - xi.y) + oh.y, dz = (xj[u].z - xi.z) + oh.z;
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < P.act2) {
-                    if (m < kShell1) {
-                        sh_d[m][t] = mk4(dx, dy, dz, r2);
-                        Sj[m] = e[u] & (int)kIndexMask;
-                    }
-                    ++m;
-                }
-            }
-        }
-        if (m > kShell1) {
-            atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
-            m = kShell1;
-        }
-        for (int a = 0; a < m; ++a) {                    // edges: pair terms, g, dg
-            const T4 d = sh_d[a][t];
-            const T r = d.w * xrsqrt(d.w);
-            T phi, dphi, g, dg;
-            sw_edge<T>(P, r, phi, dphi, g, dg);
-            sh_d[a][t] = mk4(d.x, d.y, d.z, r);
-            sh_g[a][t] = g;
-            sh_dg[a][t] = dg;
-            Sd[a] = mk4(d.x, d.y, d.z, g);
-            const T c = dphi * xrcp(r);
-            fx += c * d.x; fy += c * d.y; fz += c * d.z;
-            en += (T)0.5 * phi;
-            const T hc = (T)-0.5 * c;
-            w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
-            w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
-        }
-        for (int a = 0; a < m - 1; ++a) {                // triplets centred at i
-            const T4 da = sh_d[a][t];
-            const T ga = sh_g[a][t], dga = sh_dg[a][t];
-            const T ira = xrcp(da.w);
-            const T uax = da.x * ira, uay = da.y * ira, uaz = da.z * ira;
-            for (int bb = a + 1; bb < m; ++bb) {
-                const T4 db = sh_d[bb][t];
-                const T gb = sh_g[bb][t], dgb = sh_dg[bb][t];
-                const T irb = xrcp(db.w);
-                const T ubx = db.x * irb, uby = db.y * irb, ubz = db.z * irb;
-                const T c = uax * ubx + uay * uby + uaz * ubz;
-                const T dc = c - P.c0;
-                const T two = (T)2 * P.epslam * dc * ga * gb;
-                const T dc2 = P.epslam * dc * dc;
-                const T ta_ = two * ira, tb_ = two * irb;
-                const T fax = -(ta_ * (ubx - c * uax) + dc2 * dga * gb * uax);
-                const T fay = -(ta_ * (uby - c * uay) + dc2 * dga * gb * uay);
-                const T faz = -(ta_ * (ubz - c * uaz) + dc2 * dga * gb * uaz);
-                const T fbx = -(tb_ * (uax - c * ubx) + dc2 * ga * dgb * ubx);
-                const T fby = -(tb_ * (uay - c * uby) + dc2 * ga * dgb * uby);
-                const T fbz = -(tb_ * (uaz - c * ubz) + dc2 * ga * dgb * ubz);
-                fx -= fax + fbx; fy -= fay + fby; fz -= faz + fbz;
-                en += dc2 * ga * gb;
-                w0 += da.x * fax + db.x * fbx;
-                w1 += da.y * fay + db.y * fby;
-                w2 += da.z * faz + db.z * fbz;
-                w3 += (T)0.5 * (da.x * fay + da.y * fax + db.x * fby + db.y * fbx);
-                w4 += (T)0.5 * (da.x * faz + da.z * fax + db.x * fbz + db.z * fbx);
-                w5 += (T)0.5 * (da.y * faz + da.z * fay + db.y * fbz + db.z * fby);
-            }
-        }
-        reinterpret_cast<T4*>(b.P)[i] = mk4(fx, fy, fz, en);
-        b.shn[i] = m;
+    // 2. edges
+    for (int a = 0; a < m; ++a) {
+        const T4 d = sh_u[a][t];
+        const T ir = xrsqrt(d.w);
+        const T r = d.w * ir;
+        T phi, dphi, g, dg;
+        sw_edge<T>(P, r, phi, dphi, g, dg);
+        const T c = dphi * ir;
+        fx += c * d.x; fy += c * d.y; fz += c * d.z;
+        en += (T)0.5 * phi;
+        const T hc = (T)-0.5 * c;
+        w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
+        w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
+        sh_u[a][t] = mk4(d.x * ir, d.y * ir, d.z * ir, r);
+        sh_g[a][t] = g;
+        sh_dg[a][t] = dg;
     }
-    T red[8] = {en, (T)0, w0, w1, w2, w3, w4, w5};
-    block_sum_to_acc<T, 8>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    // 3. leg forces
+    for (int a = 0; a < m; ++a) {
+        const T4 ua = sh_u[a][t];
+        const T ga = sh_g[a][t];
+        const T k1 = (T)2 * P.epslam * ga * xrcp(ua.w);
+        const T k2 = P.epslam * sh_dg[a][t];
+        T ax = 0, ay = 0, az = 0, cc = 0, eh = 0;
+        for (int bb = 0; bb < m; ++bb) {
+            if (bb == a) continue;
+            const T4 ub = sh_u[bb][t];
+            const T gb = sh_g[bb][t];
+            const T c = ua.x * ub.x + ua.y * ub.y + ua.z * ub.z;
+            const T dc = c - P.c0;
+            const T s1 = dc * gb;
+            const T t1 = k1 * s1;
+            ax += t1 * ub.x; ay += t1 * ub.y; az += t1 * ub.z;
+            cc += t1 * c - k2 * dc * s1;
+            eh += dc * s1;
+        }
+        const T lx = cc * ua.x - ax, ly = cc * ua.y - ay, lz = cc * ua.z - az;
+        Fl[a] = mk4(lx, ly, lz, (T)0);
+        fx -= lx; fy -= ly; fz -= lz;
+        en += (T)0.5 * P.epslam * ga * eh;
+        const T dx = ua.x * ua.w, dy = ua.y * ua.w, dz = ua.z * ua.w;
+        w0 += dx * lx; w1 += dy * ly; w2 += dz * lz;
+        w3 += (T)0.5 * (dx * ly + dy * lx);
+        w4 += (T)0.5 * (dx * lz + dz * lx);
+        w5 += (T)0.5 * (dy * lz + dz * ly);
+    }
+    T4* Pa = reinterpret_cast<T4*>(b.P);
+    Pa[i] = mk4(fx, fy, fz, en);
+    Pa[b.ntot + 2 * (size_t)i] = mk4(w0, w1, w2, w3);
+    Pa[b.ntot + 2 * (size_t)i + 1] = mk4(w4, w5, (T)0, (T)0);
+    b.shn[i] = m;
 }
 
-// Force pass B, one thread per atom:
-//   F_SW(i) = P(i) + sum_{j in shell(i)} sum_{k in shell(j), k != i} -d h(j; i, k) / d x_i
-// from the stored shells (d_ji = -d_ij, g_ji = g_ij; d_jk, g_jk from j's shell).  Then, in
-// FM_SETUP / FM_STEP: Einstein springs, lambda mixing, Langevin force (this step's noise with
-// its per-system mean removed), second half kick and the kinetic sums.
+// Force pass B, L lanes per atom:
+//   F_SW(i) = P(i) + sum_{j in shell(i)} L_j(i),
+// L_j(i) being the leg force that the triplets centred on neighbour j exert on i, stored by
+// pass A at the position of i in j's shell (found by scanning j's index list; shells are
+// symmetric because both ends compute the same r^2 bit for bit).  Then, in FM_SETUP /
+// FM_STEP: Einstein springs, lambda mixing, Langevin force (this step's noise with its
+// per-system mean removed), second half kick and the kinetic sums.
 template <typename T, int MODE, int L>
 __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     using T4 = typename V4<T>::t;
@@ -1000,48 +1066,85 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
-    const int ia = part * G + grp;
     T red[14];
 #pragma unroll
     for (int k = 0; k < 14; ++k) red[k] = (T)0;
+    const int ia = part * G + grp;
     if (ia < ta.count) {
         const int i = ta.first + ia;
         const size_t N = b.ntot;
         T f[3] = {(T)0, (T)0, (T)0}, e_i = 0;
-        if (S.pot == POT_SW) {
-            const SWc<T> Pc = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
-            const T4* Sd = reinterpret_cast<const T4*>(b.shd);
-            const int m = b.shn[i];
-            // lanes share the atom's shell entries a; each walks the shell of neighbour j
-            for (int a = lane; a < m; a += L) {
-                const T4 dij = Sd[(size_t)i * kShell + a];
-                const int j = b.shj[(size_t)i * kShell + a];
-                const T r2 = dij.x * dij.x + dij.y * dij.y + dij.z * dij.z;
-                const T irji = xrsqrt(r2), rji = r2 * irji;
-                const T ux = -dij.x * irji, uy = -dij.y * irji, uz = -dij.z * irji;   // unit j -> i
-                const T gji = dij.w;
-                const T den = rji * Pc.inv_sig - Pc.a;
-                const T idn = den < -cut_eps<T>() ? xrcp(den) : (T)0;
-                const T dgji = -gji * Pc.gam * idn * idn * Pc.inv_sig;
-                const int mj = b.shn[j];
-                const T4* Sdj = Sd + (size_t)j * kShell;
-                const int* Sjj = b.shj + (size_t)j * kShell;
-#pragma unroll 4
-                for (int t = 0; t < mj; ++t) {
-                    const T4 djk = Sdj[t];
-                    if (Sjj[t] == i) continue;
-                    const T rk2 = djk.x * djk.x + djk.y * djk.y + djk.z * djk.z;
-                    const T irk = xrsqrt(rk2);
-                    const T vx = djk.x * irk, vy = djk.y * irk, vz = djk.z * irk;
-                    const T gk = djk.w;
-                    const T c = ux * vx + uy * vy + uz * vz;
-                    const T dc = c - Pc.c0;
-                    const T two = (T)2 * Pc.epslam * dc * gji * gk * irji;
-                    const T dc2 = Pc.epslam * dc * dc * dgji * gk;
-                    f[0] -= two * (vx - c * ux) + dc2 * ux;
-                    f[1] -= two * (vy - c * uy) + dc2 * uy;
-                    f[2] -= two * (vz - c * uz) + dc2 * uz;
+        // the epilogue's own-atom operands are loaded first, so their latency overlaps the gather
+        T pd[3] = {(T)0, (T)0, (T)0}, pv[3] = {(T)0, (T)0, (T)0}, pz[3] = {(T)0, (T)0, (T)0};
+        if (MODE != FM_FORCES && lane == 0) {
+            if (S.springs) {
+                const T4 d0 = reinterpret_cast<const T4*>(b.sd0)[i];
+                const T* DH = reinterpret_cast<const T*>(b.dhi);
+                const T* DL = reinterpret_cast<const T*>(b.dlo);
+                pd[0] = d0.x; pd[1] = d0.y; pd[2] = d0.z;
+                for (int k = 0; k < 3; ++k) {
+                    pd[k] += DH[k * N + i];
+                    if constexpr (sizeof(T) == 4) pd[k] += DL[k * N + i];
                 }
+            }
+            const T* V = reinterpret_cast<const T*>(b.v);
+            pv[0] = V[i]; pv[1] = V[N + i]; pv[2] = V[2 * N + i];
+            if (S.thermo) {
+                const T4 z = reinterpret_cast<const T4*>(b.xi)[i];
+                pz[0] = z.x; pz[1] = z.y; pz[2] = z.z;
+            }
+        }
+        if (S.pot == POT_SW) {
+            const T4* Fl = reinterpret_cast<const T4*>(b.shd);
+            const int m = b.shn[i];
+            // NB shell entries per lane in flight: neighbour index, the first 8 entries of the
+            // neighbour's index list (one 32-byte sector), then the leg force
+            constexpr int NB = (8 + L - 1) / L;
+            for (int base = 0; base < m; base += NB * L) {
+                int jj[NB], pos[NB];
+                int4 q0[NB], q1[NB];
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    const int a = base + u * L + lane;
+                    jj[u] = a < m ? b.shj[(size_t)i * kShell + a] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    if (jj[u] >= 0) {
+                        const int4* Sq = reinterpret_cast<const int4*>(b.shj + (size_t)jj[u] * kShell);
+                        q0[u] = Sq[0];
+                        q1[u] = Sq[1];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    pos[u] = -1;
+                    if (jj[u] < 0) continue;
+                    const int w8[8] = {q0[u].x, q0[u].y, q0[u].z, q0[u].w, q1[u].x, q1[u].y, q1[u].z, q1[u].w};
+                    bool ended = false;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        if (!ended && pos[u] < 0) {
+                            if (w8[t] == i) pos[u] = t;
+                            else if (w8[t] < 0) ended = true;
+                        }
+                    }
+                    if (pos[u] < 0 && !ended) {          // i beyond the first 8 entries of j's shell
+                        const int* Sj = b.shj + (size_t)jj[u] * kShell;
+                        for (int t = 8; t < kShell; ++t) {
+                            const int q = Sj[t];
+                            if (q == i) { pos[u] = t; break; }
+                            if (q < 0) break;
+                        }
+                    }
+                }
+                T4 lf[NB];
+#pragma unroll
+                for (int u = 0; u < NB; ++u)
+                    if (pos[u] >= 0) lf[u] = Fl[(size_t)jj[u] * kShell + pos[u]];
+#pragma unroll
+                for (int u = 0; u < NB; ++u)
+                    if (pos[u] >= 0) { f[0] += lf[u].x; f[1] += lf[u].y; f[2] += lf[u].z; }
             }
 #pragma unroll
             for (int o = L / 2; o > 0; o >>= 1) {
@@ -1049,8 +1152,14 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 f[1] += __shfl_xor_sync(gmask, f[1], o);
                 f[2] += __shfl_xor_sync(gmask, f[2], o);
             }
-            const T4 p = reinterpret_cast<const T4*>(b.P)[i];
+            const T4* Pa = reinterpret_cast<const T4*>(b.P);
+            const T4 p = Pa[i];
             f[0] += p.x; f[1] += p.y; f[2] += p.z; e_i = p.w;
+            if (lane == 0) {
+                const T4 wa = Pa[b.ntot + 2 * (size_t)i], wb = Pa[b.ntot + 2 * (size_t)i + 1];
+                red[0] = e_i;
+                red[2] = wa.x; red[3] = wa.y; red[4] = wa.z; red[5] = wa.w; red[6] = wb.x; red[7] = wb.y;
+            }
         }
         if (lane == 0) {
             if (MODE == FM_FORCES) {
@@ -1060,14 +1169,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 T fint[3] = {f[0], f[1], f[2]}, fe[3] = {(T)0, (T)0, (T)0};
                 T u_int = 0, u_ref = 0;
                 if (S.springs) {
-                    const T4 d0 = reinterpret_cast<const T4*>(b.sd0)[i];
-                    const T* DH = reinterpret_cast<const T*>(b.dhi);
-                    const T* DL = reinterpret_cast<const T*>(b.dlo);
-                    T d[3] = {d0.x, d0.y, d0.z};
-                    for (int k = 0; k < 3; ++k) {
-                        d[k] += DH[k * N + i];
-                        if constexpr (sizeof(T) == 4) d[k] += DL[k * N + i];
-                    }
+                    const T d[3] = {pd[0], pd[1], pd[2]};
                     const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                     if (S.pot == POT_EINSTEIN) {
                         const T k_i = pick<T>(S.k_int, S.kint_f);
@@ -1079,13 +1181,12 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                     for (int k = 0; k < 3; ++k) fe[k] = -k_e * d[k];
                 }
                 T* V = reinterpret_cast<T*>(b.v);
-                T v[3] = {V[i], V[N + i], V[2 * N + i]};
+                T v[3] = {pv[0], pv[1], pv[2]};
                 const T si = pick<T>(st.scale_int, st.scale_int_f), se = pick<T>(st.scale_E, st.scale_E_f);
                 T F[3];
                 for (int k = 0; k < 3; ++k) F[k] = si * fint[k] + se * fe[k];
                 if (S.thermo) {
-                    const T4 z = reinterpret_cast<const T4*>(b.xi)[i];
-                    const T zz[3] = {z.x, z.y, z.z};
+                    const T zz[3] = {pz[0], pz[1], pz[2]};
                     const T amp = pick<T>(S.amp, S.amp_f), gam = pick<T>(S.gam, S.gam_f);
                     for (int k = 0; k < 3; ++k) F[k] += -gam * v[k] + amp * (zz[k] - s_xm[k]);
                 }
@@ -1095,7 +1196,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 }
                 reinterpret_cast<T4*>(b.F)[i] = mk4(F[0], F[1], F[2], (T)0);
                 const T me = pick<T>(S.mass_e, S.mass_f);
-                red[0] = u_int;
+                red[0] += u_int;
                 red[1] = u_ref;
                 red[8] = me * v[0] * v[0];
                 red[9] = me * v[1] * v[1];
@@ -1106,8 +1207,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
             }
         }
     }
-    if (MODE != FM_FORCES)
-        block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
 
 // FP64 positions and velocities for output, and replacement from FP64 input.
@@ -1423,18 +1523,29 @@ void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_
     if (precision == NEFE_FP64) k_cells_count<double><<<g, kTile, 0, s>>>(b);
     else k_cells_count<float><<<g, kTile, 0, s>>>(b);
     k_cells_scan<<<nsys, 256, 0, s>>>(b, force_all || !b.rtiles);
-    k_cells_fill<<<g, kTile, 0, s>>>(b);
-    k_cells_sort<<<nsys, 256, 0, s>>>(b, force_all || !b.rtiles);
-    if (launches) *launches += b.rtiles ? 5 : 4;
+    if (precision == NEFE_FP64) k_cells_fill<double><<<g, kTile, 0, s>>>(b);
+    else k_cells_fill<float><<<g, kTile, 0, s>>>(b);
+    // the engine's list build ranks rows by atom index and never reads perm: the in-cell order
+    // (fixed by the sort for the stateless cell sort) does not matter there
+    if (!b.rtiles) k_cells_sort<<<nsys, 256, 0, s>>>(b, 1);
+    if (launches) *launches += 4;
 }
 
 void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
                            cudaStream_t s, long* launches) {
     if (ntiles <= 0) return;
     launch_cells(b, precision, ntiles, nsys, force_all, s, launches);
-    const int g = rebuild_grid(b, ntiles * kListLanes);
-    if (precision == NEFE_FP64) k_nlist<double><<<g, kTile, 0, s>>>(b);
-    else k_nlist<float><<<g, kTile, 0, s>>>(b);
+    const int L = (b.list_lanes == 16 || b.list_lanes == 32) ? b.list_lanes : 8;
+    const int g = rebuild_grid(b, ntiles * L);
+    if (precision == NEFE_FP64) {
+        if (L == 8) k_nlist<double, 8><<<g, kTile, 0, s>>>(b);
+        else if (L == 16) k_nlist<double, 16><<<g, kTile, 0, s>>>(b);
+        else k_nlist<double, 32><<<g, kTile, 0, s>>>(b);
+    } else {
+        if (L == 8) k_nlist<float, 8><<<g, kTile, 0, s>>>(b);
+        else if (L == 16) k_nlist<float, 16><<<g, kTile, 0, s>>>(b);
+        else k_nlist<float, 32><<<g, kTile, 0, s>>>(b);
+    }
     if (launches) *launches += 1;
 }
 
@@ -1478,14 +1589,13 @@ void launch_mirror(const Bufs& b, int precision, int ntiles, cudaStream_t s, lon
 
 template <typename T>
 static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
+    // an FP64 shell of 32 atoms per block does not fit the 48 KB static shared limit: 4 -> 8
     switch (lanes) {
-        case 1:
-            // the FP64 one-thread shells exceed the static shared limit: use 8 lanes instead
+        case 1:   // one thread per atom: FP32 only (the FP64 columns exceed the shared limit)
             if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
             else k_edges1<T><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
             break;
         case 4:
-            // the FP64 shell of 32 atoms per block does not fit the 48 KB static shared limit
             if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
             else k_edges<T, 4><<<ntiles * 4, kTile, 0, s>>>(b);
             break;
@@ -1506,8 +1616,12 @@ void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode,
 
 template <typename T, int MODE>
 static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
-    if (lanes == 1) k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b);
-    else k_gather<T, MODE, 4><<<ntiles * 4, kTile, 0, s>>>(b);
+    switch (lanes) {
+        case 1: k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b); break;
+        case 2: k_gather<T, MODE, 2><<<ntiles * 2, kTile, 0, s>>>(b); break;
+        case 8: k_gather<T, MODE, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
+        default: k_gather<T, MODE, 4><<<ntiles * 4, kTile, 0, s>>>(b); break;
+    }
 }
 
 void launch_gather(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,

@@ -22,12 +22,13 @@ struct Bufs {
     void* F;                 // total force used by the next half kick (T4)
     void* xs;                // mirror x - q h (T4)
     void* xa;                // mirror at the last build (T4)
+    void* xcs;               // mirror at the last build in cell order, atom index in .w (T4)
     void* sd0;               // anchor - r0 at the last build (T4)
     void* xi;                // thermostat noise of the current step (T4)
     void* shd;               // [ntot][kShell] in-cutoff shell: d_ij and g_ij (T4)
     int* shj;                // [ntot][kShell] shell neighbour indices
     int* shn;                // shell size
-    void* P;                 // pair + own-centred three-body force, .w = atom energy (T4)
+    void* P;                 // [ntot] pass-A force (.w = atom energy), then [ntot][2] its virial (T4)
     int4* q;                 // unwrapped cell index per axis, from the last build
     int* cell_of;
     int* perm;
@@ -48,6 +49,7 @@ struct Bufs {
     double* f_out;           // stateless: FP64 SoA forces
     double* e_atom;          // stateless: per-atom energy (may be NULL)
     int want_grad;           // pass A also sums dE/d(A, B, p, q, a, lambda3, gamma)
+    int list_lanes;          // lanes per atom of the list build (8, 16 or 32; 0: 8)
 };
 
 enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };

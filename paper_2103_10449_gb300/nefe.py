@@ -129,11 +129,13 @@ SIGNATURES = {
     "nefe_get_tuning": [_vp, _c_int_p, _c_dbl_p],
     "nefe_set_tuning": [_vp, ctypes.c_int],
     "nefe_set_gather_tuning": [_vp, ctypes.c_int],
+    "nefe_set_list_tuning": [_vp, ctypes.c_int],
     "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
     "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
     "nefe_get_state_all": [_vp, _c_dbl_p, _c_dbl_p],
     "nefe_get_results_all": [_vp, ctypes.POINTER(nefe_results), ctypes.c_int],
     "nefe_get_list_stats": [_vp, ctypes.c_int, _c_dbl_p, _c_int_p, ctypes.POINTER(ctypes.c_long)],
+    "nefe_get_shell_stats": [_vp, _c_dbl_p, _c_int_p],
     "nefe_set_profiling": [_vp, ctypes.c_int],
     "nefe_get_profile": [_vp, _c_dbl_p, ctypes.POINTER(ctypes.c_long)],
 }
@@ -373,10 +375,12 @@ class Context:
         _check(self._L.nefe_get_tuning(self.h, ctypes.byref(lanes), ctypes.byref(us)))
         return lanes.value, us.value
 
-    def set_tuning(self, lanes, gather_lanes=None):
+    def set_tuning(self, lanes, gather_lanes=None, list_lanes=None):
         _check(self._L.nefe_set_tuning(self.h, int(lanes)))
         if gather_lanes is not None:
             _check(self._L.nefe_set_gather_tuning(self.h, int(gather_lanes)))
+        if list_lanes is not None:
+            _check(self._L.nefe_set_list_tuning(self.h, int(list_lanes)))
 
     def set_state_all(self, x=None, v=None):
         """x, v: host (Ntot, 3) float64 arrays (pinned memory makes the copy faster)."""
@@ -395,6 +399,12 @@ class Context:
         m, mx, nb = ctypes.c_double(), ctypes.c_int(), ctypes.c_long()
         _check(self._L.nefe_get_list_stats(self.h, int(sys), ctypes.byref(m), ctypes.byref(mx), ctypes.byref(nb)))
         return m.value, mx.value, nb.value
+
+    def shell_stats(self):
+        mean = ctypes.c_double(0.0)
+        mx = ctypes.c_int(0)
+        _check(self._L.nefe_get_shell_stats(self.h, ctypes.byref(mean), ctypes.byref(mx)))
+        return mean.value, mx.value
 
     def set_profiling(self, enable=True):
         _check(self._L.nefe_set_profiling(self.h, int(bool(enable))))

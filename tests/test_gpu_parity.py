@@ -173,7 +173,7 @@ def _sv(T):
     return math.sqrt(O.KB * T / (O.M_SI * O.MVV2E))
 
 
-def _fl_pair(precision, nsteps=300, T=400.0, lanes=None):
+def _fl_pair(precision, nsteps=300, T=400.0, lanes=None, gather_lanes=None, list_lanes=None):
     x0, box = I.diamond(2, 2, 2)
     v0 = I.gaussian_velocities(len(x0), _sv(T), 1)
     orc = O.System(x=x0.copy(), v=v0.copy(), box=box.copy(), r0=x0.copy(), k_E=5.0, T=T, tdamp=0.1,
@@ -184,8 +184,8 @@ def _fl_pair(precision, nsteps=300, T=400.0, lanes=None):
     s = ctx.add_system(x0, box, v=v0, r0=x0)
     ctx.set_thermostat(s, T, 0.1, 9)
     ctx.set_schedule(s, nefe.NEFE_SCHED_FL, direction=1, nsteps=1000, k_E=5.0)
-    if lanes is not None:
-        ctx.set_tuning(lanes)
+    if lanes is not None or gather_lanes is not None or list_lanes is not None:
+        ctx.set_tuning(lanes if lanes is not None else 8, gather_lanes, list_lanes)
     ctx.run(nsteps)
     res = ctx.results(s)
     x, v, _ = ctx.get_state(s)
@@ -206,13 +206,30 @@ def test_frenkel_ladd_trajectory_fp64_matches_oracle(N):
     assert res["T"] == pytest.approx(ro["T"], rel=1e-7)
 
 
-@pytest.mark.parametrize("lanes", [1, 4, 8, 32])
+@pytest.mark.parametrize("lanes", [1, 4, 8, 16, 32])
 def test_frenkel_ladd_trajectory_fp32_close_to_oracle(N, lanes):
     orc, res, x, v = _fl_pair(0, nsteps=100, lanes=lanes)
     ro = orc.results()
     assert np.abs(x - orc.x).max() < 1e-4
     assert res["W"] == pytest.approx(ro["W"], rel=1e-3, abs=1e-3)
     assert res["U"] == pytest.approx(ro["U"], rel=1e-5)
+
+
+@pytest.mark.parametrize("gather_lanes", [1, 2, 4, 8])
+def test_pass_b_lanes_close_to_oracle(N, gather_lanes):
+    orc, res, x, v = _fl_pair(0, nsteps=100, gather_lanes=gather_lanes)
+    ro = orc.results()
+    assert np.abs(x - orc.x).max() < 1e-4
+    assert res["U"] == pytest.approx(ro["U"], rel=1e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_list_lanes_leave_the_run_bitwise_unchanged(N, precision):
+    """The list build's output is integer and ranked by atom index: its lane count cannot
+    change anything downstream."""
+    runs = [_fl_pair(precision, nsteps=150, list_lanes=ll) for ll in (8, 16, 32)]
+    for r in runs[1:]:
+        assert r[1]["W"] == runs[0][1]["W"] and np.array_equal(r[2], runs[0][2])
 
 
 def test_run_is_bitwise_deterministic(N):
