@@ -17,10 +17,7 @@ using namespace nefe;
 namespace {
 
 constexpr int kGraphSteps = 32;
-// The two force passes run chunk by chunk (whole systems, at most this many atoms) so that
-// the shells pass A writes are still in L2 when pass B reads them.
-constexpr int kChunkAtomsDefault = 1 << 18;
-// launches per step: group, kick-drift, 6 rebuild kernels, then 2 force passes per chunk
+// launches per step (see launches_per_step)
 int launches_per_step(const nefe_ctx* c);
 
 struct HostSys {
@@ -89,7 +86,9 @@ struct nefe_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> ev0, ev1, ev2;   // around the force passes of the captured graph
     std::vector<int> chunk_tile0, chunk_ntile;
-    int chunk_atoms = 1 << 18;   // force passes run over whole systems of at most this many atoms
+    // force passes run over whole systems of at most this many atoms per launch (one launch:
+    // splitting into L2-sized chunks was measured no faster once pass B only gathers leg forces)
+    int chunk_atoms = 1 << 30;
     std::vector<int> sys_tile0, sys_n;
     int ntiles_total = 0;
     Bufs b{};
@@ -862,15 +861,20 @@ int nefe_autotune(nefe_ctx* c) {
     cudaEvent_t e0, e1;
     NEFE_CU(cudaEventCreate(&e0));
     NEFE_CU(cudaEventCreate(&e1));
+    // best of three trials of five launches each, after two warm-up launches
     auto time_us = [&](auto&& launch) {
         for (int w = 0; w < 2; ++w) launch();
-        cudaEventRecord(e0, c->stream);
-        const int reps = 5;
-        for (int r = 0; r < reps; ++r) launch();
-        cudaEventRecord(e1, c->stream);
-        float ms = 1e30f;
-        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        return 1000.0 * ms / reps;
+        double best_trial = 1e30;
+        for (int trial = 0; trial < 3; ++trial) {
+            cudaEventRecord(e0, c->stream);
+            const int reps = 5;
+            for (int r = 0; r < reps; ++r) launch();
+            cudaEventRecord(e1, c->stream);
+            float ms = 1e30f;
+            if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            best_trial = std::min(best_trial, 1000.0 * ms / reps);
+        }
+        return best_trial;
     };
     const int cand[5] = {1, 4, 8, 16, 32};
     double best = 1e30;
@@ -895,10 +899,15 @@ int nefe_autotune(nefe_ctx* c) {
         Bufs bs = b;
         bs.v = tv;
         bs.F = tf;
+        // each variant right after pass A, as in a step (pass B reads what pass A just wrote)
         for (int l : {1, 2, 4, 8}) {
-            const double us = time_us([&] { launch_gather(bs, c->prec, l, c->ntiles, FM_STEP, c->stream, &c->launches); });
+            const double us = time_us([&] {
+                launch_edges(b, c->prec, best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
+                launch_gather(bs, c->prec, l, c->ntiles, FM_STEP, c->stream, &c->launches);
+            });
             if (us < best_g) { best_g = us; best_gl = l; }
         }
+        best_g -= best;
         NEFE_CU(cudaStreamSynchronize(c->stream));
         cudaFree(tv);
         cudaFree(tf);
@@ -906,32 +915,15 @@ int nefe_autotune(nefe_ctx* c) {
     // the list build keeps its lanes: a full rebuild (the only thing timeable here) ranks the
     // variants differently from the partial rebuilds of a run, where 8 lanes were measured best
     const int best_ll = c->llanes;
-    // chunking of the two passes (L2 residency of the shells against parallelism per launch)
-    const int old_chunk = c->chunk_atoms;
-    double best_c = 1e30;
-    int best_ca = old_chunk;
-    for (int ca : {1 << 17, 1 << 18, 1 << 19, 1 << 30}) {
-        plan_chunks(c, ca);
-        const double us = time_us([&] {
-            for (size_t k = 0; k < c->chunk_tile0.size(); ++k) {
-                Bufs bk = b;
-                bk.tile_base = c->chunk_tile0[k];
-                launch_edges(bk, c->prec, best_l, c->chunk_ntile[k], FM_FORCES, c->stream, &c->launches);
-                launch_gather(bk, c->prec, best_gl, c->chunk_ntile[k], FM_FORCES, c->stream, &c->launches);
-            }
-        });
-        if (us < best_c) { best_c = us; best_ca = ca; }
-    }
-    plan_chunks(c, best_ca);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     NEFE_CU(cudaGetLastError());
-    if (best_l != c->lanes || best_gl != c->glanes || best_ll != c->llanes || best_ca != old_chunk) drop_graph(c);
+    if (best_l != c->lanes || best_gl != c->glanes || best_ll != c->llanes) drop_graph(c);
     c->lanes = best_l;
     c->glanes = best_gl;
     c->llanes = best_ll;
     c->b.list_lanes = best_ll;
-    c->tune_us = best_c;
+    c->tune_us = best + best_g;
     return NEFE_OK;
 }
 

@@ -451,16 +451,28 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     const int cell = b.cell_of[i];
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
     const int* start = b.cell_start + S.cell0 + ta.sys;
-    // per-group table of the 27 cells (lanes share the work) and the prefix of their occupancy
+    const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
+    const T hx = pick<T>(st.h[0], st.h_f[0]), hy = pick<T>(st.h[1], st.h_f[1]), hz = pick<T>(st.h[2], st.h_f[2]);
+    // per-group table of the 27 cells (lanes share the work) and the prefix of their occupancy.
+    // A cell whose box is farther than rcs from atom i (the mirror lies in [0, h) of its own
+    // cell) holds no neighbour and is skipped; the bound is relaxed by 1e-3 of rcs^2, far
+    // above the rounding of the mirror positions, so no pair within rcs can be missed.
+    const T prune2 = (T)(S.rcs * S.rcs * 1.001);
     for (int o = lane; o < 27; o += L) {
-        int xx = cx + o % 3 - 1, yy = cy + (o / 3) % 3 - 1, zz = cz + o / 9 - 1;
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+        int xx = cx + ox, yy = cy + oy, zz = cz + oz;
         xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
         yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
         zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
         const int c2 = xx + nx * (yy + ny * zz);
         const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
+        const T ex = ox < 0 ? xi.x : (ox > 0 ? hx - xi.x : (T)0);
+        const T ey = oy < 0 ? xi.y : (oy > 0 ? hy - xi.y : (T)0);
+        const T ez = oz < 0 ? xi.z : (oz > 0 ? hz - xi.z : (T)0);
+        const T fx = ex > (T)0 ? ex : (T)0, fy = ey > (T)0 ? ey : (T)0, fz = ez > (T)0 ? ez : (T)0;
+        const bool far = fx * fx + fy * fy + fz * fz > prune2;
         cbase[grp][o] = lo;
-        cstart[grp][o + 1] = hi - lo;
+        cstart[grp][o + 1] = far ? 0 : hi - lo;
     }
     __syncwarp(gmask);
     if (lane == 0) {
@@ -470,8 +482,6 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     }
     __syncwarp(gmask);
     const int total = cstart[grp][27];
-    const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
-    const T hx = pick<T>(st.h[0], st.h_f[0]), hy = pick<T>(st.h[1], st.h_f[1]), hz = pick<T>(st.h[2], st.h_f[2]);
     T lo2, hi2;
     if constexpr (sizeof(T) == 4) {
         lo2 = S.rcs2_lo_f;
@@ -929,9 +939,9 @@ template <typename T>
 __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
-    __shared__ T4 sh_u[kShell1][NT];     // (d, r^2) after compaction, then (u, r)
-    __shared__ T sh_g[kShell1][NT];
-    __shared__ T sh_dg[kShell1][NT];
+    // 20 bytes per shell entry and thread (occupancy is bound by this table):
+    __shared__ T4 sh_u[kShell1][NT];     // (d, r^2) after compaction, then (u, g)
+    __shared__ T sh_r[kShell1][NT];      // r
     __shared__ T4 soff[27];
     const int tile = blockIdx.x / (kTile / NT) + b.tile_base, part = blockIdx.x % (kTile / NT);
     const TileAtom ta = tile_of(b, tile);
@@ -994,21 +1004,24 @@ __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
         const T hc = (T)-0.5 * c;
         w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
         w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
-        sh_u[a][t] = mk4(d.x * ir, d.y * ir, d.z * ir, r);
-        sh_g[a][t] = g;
-        sh_dg[a][t] = dg;
+        sh_u[a][t] = mk4(d.x * ir, d.y * ir, d.z * ir, g);
+        sh_r[a][t] = r;
     }
     // 3. leg forces
     for (int a = 0; a < m; ++a) {
         const T4 ua = sh_u[a][t];
-        const T ga = sh_g[a][t];
-        const T k1 = (T)2 * P.epslam * ga * xrcp(ua.w);
-        const T k2 = P.epslam * sh_dg[a][t];
+        const T ga = ua.w, ra = sh_r[a][t];
+        // dg/dr of edge a from g and r: -g gamma / (sigma (s - a)^2) (0 beyond the active cutoff)
+        const T den = ra * P.inv_sig - P.a;
+        const T ida = den < -cut_eps<T>() ? xrcp(den) : (T)0;
+        const T dga = -ga * P.gam * ida * ida * P.inv_sig;
+        const T k1 = (T)2 * P.epslam * ga * xrcp(ra);
+        const T k2 = P.epslam * dga;
         T ax = 0, ay = 0, az = 0, cc = 0, eh = 0;
         for (int bb = 0; bb < m; ++bb) {
             if (bb == a) continue;
             const T4 ub = sh_u[bb][t];
-            const T gb = sh_g[bb][t];
+            const T gb = ub.w;
             const T c = ua.x * ub.x + ua.y * ub.y + ua.z * ub.z;
             const T dc = c - P.c0;
             const T s1 = dc * gb;
@@ -1021,7 +1034,7 @@ __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
         Fl[a] = mk4(lx, ly, lz, (T)0);
         fx -= lx; fy -= ly; fz -= lz;
         en += (T)0.5 * P.epslam * ga * eh;
-        const T dx = ua.x * ua.w, dy = ua.y * ua.w, dz = ua.z * ua.w;
+        const T dx = ua.x * ra, dy = ua.y * ra, dz = ua.z * ra;
         w0 += dx * lx; w1 += dy * ly; w2 += dz * lz;
         w3 += (T)0.5 * (dx * ly + dy * lx);
         w4 += (T)0.5 * (dx * lz + dz * lx);
