@@ -263,6 +263,43 @@ def differentiation_throughput(N, torch):
     return out
 
 
+def dcci_batched_throughput(N, torch, pairs=64, steps=5):
+    """The batched dCCI workload: `pairs` coupled Si-cd / beta-Sn pairs of uneven sizes
+    (log-uniform 512..32768 atoms per phase, from a fixed seed) in one context, pressure-
+    controlled coexistence integration from 10 GPa at 400 K (Eq. l_coex_discreted), FP32
+    kernels, captured graph; atom-steps/s over `steps` graph replays after equilibration and
+    autotuning."""
+    from paper_2103_10449_gb300 import inputs as I
+    sizes = I.log_uniform_sizes(pairs, 512, 32768, seed=2021)
+    sv = math.sqrt(KB * 400.0 / (MASS * MVV2E))
+    stream = torch.cuda.Stream()
+    ctx = N.Context(precision=N.NEFE_FP32, dt=0.001, skin=SKIN, nbr_cap=48, stream=stream)
+    natoms = 0
+    for k, n in enumerate(sizes):
+        xa, ba = I.diamond(*I.diamond_cells_for(n))
+        xb, bb = I.beta_tin(*I.beta_tin_cells_for(n))
+        a = ctx.add_system(xa, ba, v=I.gaussian_velocities(len(xa), sv, 3000 + 2 * k), mass=MASS)
+        b = ctx.add_system(xb, bb, v=I.gaussian_velocities(len(xb), sv, 3001 + 2 * k), mass=MASS)
+        for sidx, seed in ((a, 3000 + 2 * k), (b, 3001 + 2 * k)):
+            ctx.set_thermostat(sidx, 400.0, 0.1, seed)
+        ctx.set_barostat(a, N.NEFE_BARO_ISO, 10.0, 0.5)
+        ctx.set_barostat(b, N.NEFE_BARO_ANISO, 10.0, 0.5)
+        ctx.pair_dcci(a, b, 400.0, 10.0, N.NEFE_DCCI_PRESS, 10.0, 15.0, 100000)
+        natoms += len(xa) + len(xb)
+    ctx.setup()
+    ctx.run(320)
+    ctx.autotune()
+    ctx.run(2 * MD_STEPS)
+    ctx.sync()
+    wall = time_steps(torch, ctx, stream, steps, MD_STEPS)
+    errors = sum(1 for r in ctx.results_all() if r["error"] != 0)
+    ctx.close()
+    return {"workload": f"{pairs} Si-cd/beta-Sn dCCI pairs, 512..32768 atoms per phase (log-uniform), "
+                        f"pressure control 10 -> 15 GPa at 400 K, FP32 kernels",
+            "atoms": natoms, "atom_steps_per_s": natoms * MD_STEPS * steps / wall,
+            "systems_with_errors": errors}
+
+
 def time_steps(torch, ctx, stream, steps, md_steps):
     """Seconds for `steps` timed steps, from CUDA events on the context's stream."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -457,6 +494,7 @@ def main():
         line["comparators"] = comp
         line["dG_err"] = free_energy_error(N)
         line["differentiation"] = differentiation_throughput(N, torch)
+        line["dcci_batched"] = dcci_batched_throughput(N, torch)
         cps, nst, dt = cpu_baseline_sample()
         line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{nst} FP64-oracle MD steps of one 8000-atom replica ({dt:.1f} s)"}
