@@ -425,16 +425,16 @@ __device__ __noinline__ bool exact_pair_in(const Bufs& b, const double box[3], i
     return rr < rcs2;
 }
 
-// R5: Verlet list, kListLanes lanes per atom.  The candidates of the 27 neighbour cells
-// (cell offset o in {-1,0,1}^3) are dealt over the lanes; a candidate is accepted or
-// rejected on its mirror distance when that lies outside a relative band of 1e-4 (FP32) /
-// 1e-10 (FP64) around rcs^2, and inside the band by the exact FP64 criterion (which must
-// also agree with the offset's image), so the list equals the plain definition bit for
-// bit.  Accepted entries are ranked by atom index (a rank count, no atomics) into the row.
+// R5: Verlet list, L lanes per atom.  Lane l walks neighbour cells l, l + L, ... (cell
+// offset o in {-1,0,1}^3) and their atoms, which sit contiguously in the cell-ordered mirror
+// copy.  A candidate is accepted or rejected on its mirror distance when that lies outside a
+// relative band of 1e-4 (FP32) / 1e-10 (FP64) around rcs^2, and inside the band by the exact
+// FP64 criterion (which must also agree with the offset's image), so the list equals the
+// plain definition bit for bit.  Accepted entries are appended in any order (a shared
+// counter) and then ranked by atom index into the row, which fixes the order.
 constexpr int kRebuildBlocks = 152 * 8;   // bounded grid of the worklist-driven rebuild kernels
 template <typename T, int L>
-__device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap + 1], int (*cstart)[28],
-                           int (*cbase)[27]) {
+__device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap + 1], int* cnt_s) {
     using T4 = typename V4<T>::t;
     constexpr int G = kTile / L;
     const TileAtom ta = tile_of(b, tile);
@@ -453,35 +453,6 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     const int* start = b.cell_start + S.cell0 + ta.sys;
     const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
     const T hx = pick<T>(st.h[0], st.h_f[0]), hy = pick<T>(st.h[1], st.h_f[1]), hz = pick<T>(st.h[2], st.h_f[2]);
-    // per-group table of the 27 cells (lanes share the work) and the prefix of their occupancy.
-    // A cell whose box is farther than rcs from atom i (the mirror lies in [0, h) of its own
-    // cell) holds no neighbour and is skipped; the bound is relaxed by 1e-3 of rcs^2, far
-    // above the rounding of the mirror positions, so no pair within rcs can be missed.
-    const T prune2 = (T)(S.rcs * S.rcs * 1.001);
-    for (int o = lane; o < 27; o += L) {
-        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-        int xx = cx + ox, yy = cy + oy, zz = cz + oz;
-        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-        const int c2 = xx + nx * (yy + ny * zz);
-        const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
-        const T ex = ox < 0 ? xi.x : (ox > 0 ? hx - xi.x : (T)0);
-        const T ey = oy < 0 ? xi.y : (oy > 0 ? hy - xi.y : (T)0);
-        const T ez = oz < 0 ? xi.z : (oz > 0 ? hz - xi.z : (T)0);
-        const T fx = ex > (T)0 ? ex : (T)0, fy = ey > (T)0 ? ey : (T)0, fz = ez > (T)0 ? ez : (T)0;
-        const bool far = fx * fx + fy * fy + fz * fz > prune2;
-        cbase[grp][o] = lo;
-        cstart[grp][o + 1] = far ? 0 : hi - lo;
-    }
-    __syncwarp(gmask);
-    if (lane == 0) {
-        cstart[grp][0] = 0;
-        for (int o = 1; o <= 27; ++o) cstart[grp][o] += cstart[grp][o - 1];
-        for (int o = 0; o < 27; ++o) cbase[grp][o] -= cstart[grp][o];   // p = cbase[o] + f
-    }
-    __syncwarp(gmask);
-    const int total = cstart[grp][27];
     T lo2, hi2;
     if constexpr (sizeof(T) == 4) {
         lo2 = S.rcs2_lo_f;
@@ -490,62 +461,59 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
         lo2 = S.rcs * S.rcs * (1.0 - 1e-10);
         hi2 = S.rcs * S.rcs * (1.0 + 1e-10);
     }
-    const int cap = b.cap;
-    // candidates in cell order: consecutive candidates of a cell are consecutive in xcs
+    // A cell whose box is farther than rcs from atom i (the mirror lies in [0, h) of its own
+    // cell) holds no neighbour and is skipped; the bound is relaxed by 1e-3 of rcs^2, far
+    // above the rounding of the mirror positions, so no pair within rcs can be missed.
+    const T prune2 = (T)(S.rcs * S.rcs * 1.001);
     const T4* xc = reinterpret_cast<const T4*>(b.xcs) + S.off;
-    int count = 0;
-    int o = 0;
-    constexpr int NB = 2;
-    for (int base = 0; base < total; base += NB * L) {
-        T4 xj[NB];
-        int oo[NB];
-#pragma unroll
-        for (int u = 0; u < NB; ++u) {
-            const int f = base + u * L + lane;
-            oo[u] = -1;
-            if (f < total) {
-                while (f >= cstart[grp][o + 1]) ++o;
-                oo[u] = o;
-                const int p = cbase[grp][o] + f;
-                xj[u] = xc[p < 0 ? 0 : (p >= S.n ? S.n - 1 : p)];
+    if (lane == 0) cnt_s[grp] = 0;
+    __syncwarp(gmask);
+    for (int o = lane; o < 27; o += L) {
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+        const T ex = ox < 0 ? xi.x : (ox > 0 ? hx - xi.x : (T)0);
+        const T ey = oy < 0 ? xi.y : (oy > 0 ? hy - xi.y : (T)0);
+        const T ez = oz < 0 ? xi.z : (oz > 0 ? hz - xi.z : (T)0);
+        const T fx = ex > (T)0 ? ex : (T)0, fy = ey > (T)0 ? ey : (T)0, fz = ez > (T)0 ? ez : (T)0;
+        if (fx * fx + fy * fy + fz * fz > prune2) continue;
+        int xx = cx + ox, yy = cy + oy, zz = cz + oz;
+        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        const int c2 = xx + nx * (yy + ny * zz);
+        const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
+        const T offx = (T)ox * hx, offy = (T)oy * hy, offz = (T)oz * hz;
+#pragma unroll 2
+        for (int p = lo; p < hi; ++p) {
+            const T4 xj = xc[p];
+            const int j = unpack_index(xj.w);
+            if (j < S.off || j >= S.off + S.n) {
+                atomicOr(&st.err, NEFE_ERR_CELL);
+                continue;
             }
-        }
-#pragma unroll
-        for (int u = 0; u < NB; ++u) {
+            if (j == i && o == 13) continue;
+            const T dx = xj.x - xi.x + offx;
+            const T dy = xj.y - xi.y + offy;
+            const T dz = xj.z - xi.z + offz;
+            const T dd = dx * dx + dy * dy + dz * dz;
             bool in = false;
-            int e = 0;
-            const int ou = oo[u];
-            if (ou >= 0) {
-                const int j = unpack_index(xj[u].w);
-                const int ox = ou % 3 - 1, oy = (ou / 3) % 3 - 1, oz = ou / 9 - 1;
-                if (j < S.off || j >= S.off + S.n) {
-                    atomicOr(&st.err, NEFE_ERR_CELL);
-                } else if (!(j == i && ou == 13)) {
-                    const T dx = xj[u].x - xi.x + (T)ox * hx;
-                    const T dy = xj[u].y - xi.y + (T)oy * hy;
-                    const T dz = xj[u].z - xi.z + (T)oz * hz;
-                    const T dd = dx * dx + dy * dy + dz * dz;
-                    if (dd < lo2) {
-                        in = true;
-                    } else if (dd <= hi2) {
-                        double d[3];
-                        in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
-                        in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
-                             fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
-                             fabs(d[2] - (double)dz) < 0.5 * st.h[2];
-                    }
-                    e = j | (ou << kCodeShift);
-                }
+            if (dd < lo2) {
+                in = true;
+            } else if (dd <= hi2) {
+                double d[3];
+                in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
+                in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
+                     fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
+                     fabs(d[2] - (double)dz) < 0.5 * st.h[2];
             }
-            const unsigned bal = __ballot_sync(gmask, in);
             if (in) {
-                const int pos = count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
-                if (pos < kMaxCap) buf[grp][pos] = e;
+                const int pos = atomicAdd(&cnt_s[grp], 1);
+                if (pos < kMaxCap) buf[grp][pos] = j | (o << kCodeShift);
             }
-            count += __popc(bal);
         }
     }
     __syncwarp(gmask);
+    const int count = cnt_s[grp];
+    const int cap = b.cap;
     // rank by atom index into the row (indices in a row are distinct)
     const int m = count < cap ? count : cap;
     const int have = count < kMaxCap ? count : kMaxCap;
@@ -568,14 +536,13 @@ template <typename T, int L>
 __global__ void __launch_bounds__(kTile) k_nlist(Bufs b) {
     constexpr int G = kTile / L;
     __shared__ int buf[G][kMaxCap + 1];   // padded: the groups of a warp on different banks
-    __shared__ int cstart[G][28];
-    __shared__ int cbase[G][27];
+    __shared__ int cnt_s[G];
     if (b.rtiles) {
         const int n = *b.rcount * L;
         for (int w = blockIdx.x; w < n; w += gridDim.x)
-            nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cstart, cbase);
+            nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cnt_s);
     } else {
-        nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, buf, cstart, cbase);
+        nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, buf, cnt_s);
     }
 }
 
