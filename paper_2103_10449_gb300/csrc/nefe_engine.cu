@@ -66,7 +66,7 @@ struct nefe_ctx {
     double *d_x = nullptr, *d_r0 = nullptr, *d_ftmp = nullptr, *d_vtmp = nullptr;
     void *d_v = nullptr, *d_dhi = nullptr, *d_dlo = nullptr;
     void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_xcs = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
-    void *d_shd = nullptr, *d_P = nullptr;
+    void *d_shd = nullptr, *d_P = nullptr, *d_spill = nullptr;
     int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr;
     int4* d_q = nullptr;
     int *d_cell_of = nullptr, *d_perm = nullptr, *d_cell_start = nullptr, *d_cell_count = nullptr,
@@ -363,6 +363,8 @@ int setup(nefe_ctx* c) {
     if ((rc = dalloc(c, &c->d_sd0, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_xi, v4 * N))) return rc;
     if ((rc = dalloc(c, &c->d_shd, v4 * N * (size_t)kShell))) return rc;
+    // spill area of the thread-per-atom pass A (FP32 only): the last kSpill1 entries of a shell
+    if (c->prec == NEFE_FP32 && (rc = dalloc(c, &c->d_spill, (v4 + sizeof(float)) * N * kSpill1))) return rc;
     if ((rc = dalloc(c, &c->d_shj, sizeof(int) * N * (size_t)kShell))) return rc;
     if ((rc = dalloc(c, &c->d_shn, sizeof(int) * N))) return rc;
     if ((rc = dalloc(c, &c->d_P, 3 * v4 * N))) return rc;
@@ -423,7 +425,7 @@ int setup(nefe_ctx* c) {
     b.sys = c->d_sys; b.st = c->d_st; b.acc = c->d_acc; b.tile_sys = c->d_tile_sys;
     b.x = c->d_x; b.v = c->d_v; b.dhi = c->d_dhi; b.dlo = c->d_dlo; b.r0 = c->d_r0; b.F = c->d_F;
     b.xs = c->d_xs; b.xa = c->d_xa; b.xcs = c->d_xcs; b.sd0 = c->d_sd0; b.xi = c->d_xi;
-    b.shd = c->d_shd; b.shj = c->d_shj; b.shn = c->d_shn; b.P = c->d_P;
+    b.shd = c->d_shd; b.shj = c->d_shj; b.shn = c->d_shn; b.P = c->d_P; b.spill = c->d_spill;
     b.rtiles = c->d_rtiles; b.rcount = c->d_rcount;
     b.q = c->d_q; b.cell_of = c->d_cell_of; b.perm = c->d_perm; b.cell_start = c->d_cell_start;
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;

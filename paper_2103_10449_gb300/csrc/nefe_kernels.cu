@@ -898,17 +898,23 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
 }
 
 // Force pass A, one thread per atom (64-thread blocks, half a tile each), FP32: the same
-// three phases as k_edges with the shell in shared memory, one column per thread (kShell1
-// entries), and no lane coordination (no ballots, no idle lanes while another holds edges).
-constexpr int kShell1 = 20;
+// three phases as k_edges with no lane coordination (no ballots, no idle lanes while another
+// holds edges).  The shell is a column per thread: its first kShell1Shared entries in shared
+// memory (20 bytes each; this table bounds the occupancy, so it is sized for the typical
+// shell), the rest up to kShell1 in a per-atom spill area in global memory (b.spill; without
+// one the capacity is kShell1Shared).  Loop counters are equal across a warp, so the choice
+// between the two places is uniform.
+constexpr int kShell1Shared = 12;
+constexpr int kShell1 = kShell1Shared + kSpill1;
 constexpr int kEdges1Threads = 64;
 template <typename T>
 __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
     // 20 bytes per shell entry and thread (occupancy is bound by this table):
-    __shared__ T4 sh_u[kShell1][NT];     // (d, r^2) after compaction, then (u, g)
-    __shared__ T sh_r[kShell1][NT];      // r
+    constexpr int K1 = kShell1Shared, KS = kShell1 - kShell1Shared;
+    __shared__ T4 sh_u[K1][NT];          // (d, r^2) after compaction, then (u, g)
+    __shared__ T sh_r[K1][NT];           // r
     __shared__ T4 soff[27];
     const int tile = blockIdx.x / (kTile / NT) + b.tile_base, part = blockIdx.x % (kTile / NT);
     const TileAtom ta = tile_of(b, tile);
@@ -926,6 +932,14 @@ __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
     const int* row = b.nbr + (size_t)i * b.cap;
     T4* Fl = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
     int* Sj = b.shj + (size_t)i * kShell;
+    T4* spu = b.spill ? reinterpret_cast<T4*>(b.spill) + (size_t)i * KS : nullptr;
+    T* spr = b.spill ? reinterpret_cast<T*>(reinterpret_cast<T4*>(b.spill) + (size_t)b.ntot * KS) + (size_t)i * KS
+                     : nullptr;
+    const int capm = b.spill ? kShell1 : K1;
+    auto put_u = [&](int a, T4 v) { if (a < K1) sh_u[a][t] = v; else spu[a - K1] = v; };
+    auto get_u = [&](int a) -> T4 { return a < K1 ? sh_u[a][t] : spu[a - K1]; };
+    auto put_r = [&](int a, T v) { if (a < K1) sh_r[a][t] = v; else spr[a - K1] = v; };
+    auto get_r = [&](int a) -> T { return a < K1 ? sh_r[a][t] : spr[a - K1]; };
     // 1. compaction, four row entries in flight
     int m = 0;
     for (int base = 0; base < ci; base += 4) {
@@ -943,24 +957,24 @@ __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
             const T dx = (xj[u].x - xi.x) + oh.x, dy = (xj[u].y - xi.y) + oh.y, dz = (xj[u].z - xi.z) + oh.z;
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < P.act2) {
-                if (m < kShell1) {
-                    sh_u[m][t] = mk4(dx, dy, dz, r2);
+                if (m < capm) {
+                    put_u(m, mk4(dx, dy, dz, r2));
                     Sj[m] = e[u] & (int)kIndexMask;
                 }
                 ++m;
             }
         }
     }
-    if (m > kShell1) {
+    if (m > capm) {
         atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
-        m = kShell1;
+        m = capm;
     }
     if (m < kShell) Sj[m] = -1;
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     // 2. edges
     for (int a = 0; a < m; ++a) {
-        const T4 d = sh_u[a][t];
+        const T4 d = get_u(a);
         const T ir = xrsqrt(d.w);
         const T r = d.w * ir;
         T phi, dphi, g, dg;
@@ -971,13 +985,13 @@ __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
         const T hc = (T)-0.5 * c;
         w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
         w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
-        sh_u[a][t] = mk4(d.x * ir, d.y * ir, d.z * ir, g);
-        sh_r[a][t] = r;
+        put_u(a, mk4(d.x * ir, d.y * ir, d.z * ir, g));
+        put_r(a, r);
     }
     // 3. leg forces
     for (int a = 0; a < m; ++a) {
-        const T4 ua = sh_u[a][t];
-        const T ga = ua.w, ra = sh_r[a][t];
+        const T4 ua = get_u(a);
+        const T ga = ua.w, ra = get_r(a);
         // dg/dr of edge a from g and r: -g gamma / (sigma (s - a)^2) (0 beyond the active cutoff)
         const T den = ra * P.inv_sig - P.a;
         const T ida = den < -cut_eps<T>() ? xrcp(den) : (T)0;
@@ -987,7 +1001,7 @@ __global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
         T ax = 0, ay = 0, az = 0, cc = 0, eh = 0;
         for (int bb = 0; bb < m; ++bb) {
             if (bb == a) continue;
-            const T4 ub = sh_u[bb][t];
+            const T4 ub = get_u(bb);
             const T gb = ub.w;
             const T c = ua.x * ub.x + ua.y * ub.y + ua.z * ub.z;
             const T dc = c - P.c0;

@@ -28,6 +28,7 @@ struct Bufs {
     void* shd;               // [ntot][kShell] in-cutoff shell: d_ij and g_ij (T4)
     int* shj;                // [ntot][kShell] shell neighbour indices
     int* shn;                // shell size
+    void* spill;             // thread-per-atom pass A: shell entries beyond its shared table, or NULL
     void* P;                 // [ntot] pass-A force (.w = atom energy), then [ntot][2] its virial (T4)
     int4* q;                 // unwrapped cell index per axis, from the last build
     int* cell_of;

@@ -236,3 +236,27 @@ def test_run_is_bitwise_deterministic(N):
     a = _fl_pair(0, nsteps=200)
     b = _fl_pair(0, nsteps=200)
     assert a[1]["W"] == b[1]["W"] and np.array_equal(a[2], b[2])
+
+
+def test_thread_per_atom_pass_a_with_spilled_shells(N):
+    """A random liquid has in-cutoff shells beyond the 12 entries the one-thread-per-atom pass A
+    keeps in shared memory; the rest live in its global spill area.  Ten FP32 steps against the
+    FP64 oracle (NVT, 1700 K)."""
+    x0, box = I.liquid(512, 0.05425, seed=81)
+    v0 = I.gaussian_velocities(len(x0), _sv(1700.0), 82)
+    orc = O.System(x=x0.copy(), v=v0.copy(), box=box.copy(), T=1700.0, tdamp=0.1, seed=83, sys_id=0)
+    orc.run(10)
+    from paper_2103_10449_gb300 import nefe
+    ctx = nefe.Context(precision=nefe.NEFE_FP32, skin=SKIN, nbr_cap=CAP)
+    s = ctx.add_system(x0, box, v=v0)
+    ctx.set_thermostat(s, 1700.0, 0.1, 83)
+    ctx.set_tuning(1)
+    ctx.run(10)
+    _, mx = ctx.shell_stats()
+    res = ctx.results(s)
+    x, v, _ = ctx.get_state(s)
+    ctx.close()
+    assert mx > 12
+    assert res["error"] == 0
+    assert np.abs(x - orc.x).max() < 1e-4
+    assert res["U"] == pytest.approx(orc.results()["U"], rel=1e-5)
