@@ -372,6 +372,8 @@ def main():
     ap.add_argument("--equil", type=int, default=3000,
                     help="untimed MD steps before warm-up (thermalises the crystals)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
+    ap.add_argument("--tuning", default=None,
+                    help="pass A,pass B lanes per atom instead of autotuning (e.g. to profile a chosen configuration)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -398,7 +400,11 @@ def main():
     from paper_2103_10449_gb300 import sharding as SH
     ctx, natoms = build_context(N, R, N.NEFE_FP32, seed0=SH.rank_seed(1000, rank), stream=stream)
     ctx.run(args.equil)
-    lanes, tune_us = ctx.autotune()
+    if args.tuning:
+        la, lb = (int(v) for v in args.tuning.split(","))
+        ctx.set_tuning(la, lb)
+    else:
+        ctx.autotune()
     ctx.set_profiling(True)
     for _ in range(args.warmup):
         ctx.run(MD_STEPS)
@@ -443,7 +449,8 @@ def main():
                 "pass_a_us_mean": a_us, "pass_b_us_mean": b_us,
                 "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak,
                 "step_bytes_per_atom_step": STEP_BYTES,
-                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "lanes_per_atom": lanes}
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "lanes_per_atom": ctx.lanes()[0],
+                "lanes_pass_a_pass_b_list": list(ctx.lanes())}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,

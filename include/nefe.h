@@ -332,11 +332,18 @@ NEFE_API int nefe_load(nefe_ctx* ctx, const char* path);
 
 /* Times the variants of both force passes on the current state and keeps the fastest:
  * pass A with 1 (one thread per atom), 4, 8, 16 or 32 lanes per atom (FP64: 8, 16, 32),
- * pass B with 1, 2, 4 or 8 lanes per atom (the list build keeps its lanes, 8 unless set).  nefe_get_tuning reports pass A's lanes and the summed
- * time of the two chosen passes; nefe_set_tuning fixes pass A's lanes. */
+ * pass B with 1, 2, 4 or 8 lanes per atom (the list build keeps its lanes, 8 unless set).
+ * Each kernel is first timed alone; then the two fastest pass-A variants with every pass-B
+ * variant run as real steps on a device snapshot of the state, restored afterwards (the run
+ * continues bit for bit as without the call; the snapshot needs about as much free device
+ * memory as the state, and without it the kernel-level choice stands).  nefe_get_tuning
+ * reports pass A's lanes and the time per MD step of the chosen pair (kernel-level: the two
+ * passes' summed time); nefe_set_tuning fixes pass A's lanes.  Blocking. */
 NEFE_API int nefe_autotune(nefe_ctx* ctx);
 NEFE_API int nefe_get_tuning(nefe_ctx* ctx, int* lanes_per_atom, double* best_us);
 NEFE_API int nefe_set_tuning(nefe_ctx* ctx, int lanes_per_atom);
+/* Lanes per atom in use: [0] pass A, [1] pass B, [2] list build. */
+NEFE_API int nefe_get_lanes(nefe_ctx* ctx, int lanes[3]);
 /* Fixes pass B's lanes per atom (1, 2, 4 or 8). */
 NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
 /* Fixes the list build's lanes per atom (8, 16 or 32). */

@@ -851,6 +851,70 @@ int nefe_load(nefe_ctx* c, const char* path) {
     return ok ? NEFE_OK : fail(NEFE_EINVAL, "nefe_load: truncated or unreadable checkpoint");
 }
 
+// Step-level refinement of the kernel-level choice: the two fastest pass-A variants with each
+// pass-B variant run as real captured steps (2 x kGraphSteps, timed after one warm replay) on
+// a device snapshot of the whole dynamic state (the checkpoint blobs), which is restored after
+// every candidate, so the context continues bit for bit where it was.  A kernel timed alone
+// can rank the variants differently from the same kernel inside the step.  Without memory for
+// the snapshot the kernel-level choice stands.
+static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>>& ranked_a) {
+    const std::vector<Blob> bl = blobs(c);
+    size_t total = 0;
+    for (const Blob& x : bl) total += (x.bytes + 255) / 256 * 256;
+    char* snap = nullptr;
+    if (cudaMalloc(&snap, total) != cudaSuccess) {
+        cudaGetLastError();
+        return NEFE_OK;
+    }
+    auto copy = [&](bool save) {
+        size_t off = 0;
+        for (const Blob& x : bl) {
+            if (save) cudaMemcpyAsync(snap + off, x.p, x.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            else cudaMemcpyAsync(x.p, snap + off, x.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            off += (x.bytes + 255) / 256 * 256;
+        }
+    };
+    copy(true);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = c->profiling;
+    c->profiling = false;
+    const long launches = c->launches;
+    double best = 1e30;
+    int best_a = c->lanes, best_b = c->glanes;
+    int rc = NEFE_OK;
+    for (size_t ka = 0; ka < ranked_a.size() && ka < 2 && rc == NEFE_OK; ++ka) {
+        for (int lb : {1, 2, 4, 8}) {
+            c->lanes = ranked_a[ka].second;
+            c->glanes = lb;
+            drop_graph(c);
+            if ((rc = nefe_run(c, kGraphSteps))) break;
+            cudaEventRecord(e0, c->stream);
+            if ((rc = nefe_run(c, 2 * kGraphSteps))) break;
+            cudaEventRecord(e1, c->stream);
+            float ms = 1e30f;
+            if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            const double us = 1000.0 * ms / (2 * kGraphSteps);
+            if (us < best) { best = us; best_a = ranked_a[ka].second; best_b = lb; }
+            copy(false);
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    c->profiling = prof;
+    c->launches = launches;
+    drop_graph(c);
+    if (rc) return rc;
+    c->lanes = best_a;
+    c->glanes = best_b;
+    c->tune_us = best;
+    NEFE_CU(cudaGetLastError());
+    return NEFE_OK;
+}
+
 int nefe_autotune(nefe_ctx* c) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     int rc = setup(c);
@@ -881,11 +945,14 @@ int nefe_autotune(nefe_ctx* c) {
     const int cand[5] = {1, 4, 8, 16, 32};
     double best = 1e30;
     int best_l = c->lanes;
+    std::vector<std::pair<double, int>> ranked_a;   // (time, lanes) of every pass-A variant
     for (int l : cand) {
         if (c->prec == NEFE_FP64 && (l == 1 || l == 4)) continue;
         const double us = time_us([&] { launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches); });
+        ranked_a.push_back({us, l});
         if (us < best) { best = us; best_l = l; }
     }
+    std::sort(ranked_a.begin(), ranked_a.end());
     launch_edges(b, c->prec, best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
     double best_g = 1e30;
     int best_gl = c->glanes;
@@ -926,6 +993,14 @@ int nefe_autotune(nefe_ctx* c) {
     c->llanes = best_ll;
     c->b.list_lanes = best_ll;
     c->tune_us = best + best_g;
+    return refine_in_steps(c, ranked_a);
+}
+
+int nefe_get_lanes(nefe_ctx* c, int lanes[3]) {
+    if (!c || !lanes) return fail(NEFE_EINVAL, "NULL argument");
+    lanes[0] = c->lanes;
+    lanes[1] = c->glanes;
+    lanes[2] = c->llanes;
     return NEFE_OK;
 }
 

@@ -129,6 +129,7 @@ SIGNATURES = {
     "nefe_get_tuning": [_vp, _c_int_p, _c_dbl_p],
     "nefe_set_tuning": [_vp, ctypes.c_int],
     "nefe_set_gather_tuning": [_vp, ctypes.c_int],
+    "nefe_get_lanes": [_vp, _c_int_p],
     "nefe_set_list_tuning": [_vp, ctypes.c_int],
     "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
     "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
@@ -374,6 +375,12 @@ class Context:
         lanes, us = ctypes.c_int(), ctypes.c_double()
         _check(self._L.nefe_get_tuning(self.h, ctypes.byref(lanes), ctypes.byref(us)))
         return lanes.value, us.value
+
+    def lanes(self):
+        """(pass A, pass B, list build) lanes per atom in use."""
+        out = (ctypes.c_int * 3)()
+        _check(self._L.nefe_get_lanes(self.h, out))
+        return tuple(out[:])
 
     def set_tuning(self, lanes, gather_lanes=None, list_lanes=None):
         _check(self._L.nefe_set_tuning(self.h, int(lanes)))

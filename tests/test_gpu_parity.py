@@ -260,3 +260,38 @@ def test_thread_per_atom_pass_a_with_spilled_shells(N):
     assert res["error"] == 0
     assert np.abs(x - orc.x).max() < 1e-4
     assert res["U"] == pytest.approx(orc.results()["U"], rel=1e-5)
+
+
+def test_autotune_leaves_the_run_unchanged(N):
+    """The autotuner's step-level timing runs on a snapshot that it restores: a run that
+    autotunes midway equals, bit for bit, one that sets the chosen lanes by hand."""
+    from paper_2103_10449_gb300 import nefe
+    x0, box = I.diamond(4, 4, 4)
+    v0 = I.gaussian_velocities(len(x0), _sv(1000.0), 91)
+
+    def make():
+        ctx = nefe.Context(precision=nefe.NEFE_FP32, skin=SKIN, nbr_cap=CAP)
+        for r in range(3):
+            s = ctx.add_system(x0, box, v=v0, r0=x0)
+            ctx.set_thermostat(s, 1000.0, 0.1, 92 + r)
+            ctx.set_schedule(s, nefe.NEFE_SCHED_FL, nsteps=500, k_E=5.0)
+        return ctx
+    a = make()
+    a.run(64)
+    a.autotune()
+    la = a.lanes()
+    a.run(64)
+    ra = a.results_all()
+    xa = [a.get_state(s)[0] for s in range(3)]
+    a.close()
+    b = make()
+    b.run(64)
+    b.set_tuning(la[0], la[1], la[2])
+    b.run(64)
+    rb = b.results_all()
+    xb = [b.get_state(s)[0] for s in range(3)]
+    b.close()
+    for s in range(3):
+        assert ra[s]["step"] == rb[s]["step"] == 128
+        assert ra[s]["W"] == rb[s]["W"]
+        assert np.array_equal(xa[s], xb[s])
