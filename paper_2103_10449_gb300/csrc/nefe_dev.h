@@ -12,7 +12,7 @@ constexpr double kEvA3ToGPa = 160.21766340;   // 1 eV/A^3 in GPa (1.602176634e-1
 
 constexpr int kTile = 128;        // atoms per tile; a tile never straddles two systems
 constexpr int kShell = 32;        // max neighbours inside a*sigma held per atom
-constexpr int kSpill1 = 8;        // thread-per-atom pass A: shell entries kept in global memory
+constexpr int kSpill1 = 12;       // thread-per-atom pass A: shell entries kept in global memory
 constexpr int kMaxCap = 64;       // max neighbour row capacity (one 64-bit slot mask per atom)
 constexpr int kCodeShift = 27;    // nbr entry = j | (cell-offset code << 27)
 constexpr uint32_t kIndexMask = (1u << kCodeShift) - 1u;

@@ -904,11 +904,11 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
 // shell), the rest up to kShell1 in a per-atom spill area in global memory (b.spill; without
 // one the capacity is kShell1Shared).  Loop counters are equal across a warp, so the choice
 // between the two places is uniform.
-constexpr int kShell1Shared = 12;
+constexpr int kShell1Shared = 8;
 constexpr int kShell1 = kShell1Shared + kSpill1;
 constexpr int kEdges1Threads = 64;
 template <typename T>
-__global__ void __launch_bounds__(kEdges1Threads) k_edges1(Bufs b) {
+__global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
     // 20 bytes per shell entry and thread (occupancy is bound by this table):
