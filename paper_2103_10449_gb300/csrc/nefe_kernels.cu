@@ -1093,7 +1093,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
             const int m = b.shn[i];
             // NB shell entries per lane in flight: neighbour index, the first 8 entries of the
             // neighbour's index list (one 32-byte sector), then the leg force
-            constexpr int NB = L >= 4 ? 1 : 4 / L;
+            constexpr int NB = L >= 2 ? 1 : 2;
             for (int base = 0; base < m; base += NB * L) {
                 int jj[NB], pos[NB];
                 int4 q0[NB], q1[NB];
