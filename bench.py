@@ -56,12 +56,12 @@ PASS_B_FIXED = 16 + 4 + 16 + 24 + 16 + 12 + 12 + 16
 STEP_BYTES = 212.0
 
 
-def workload_config(replicas):
+def workload_config(replicas, skin=SKIN):
     return {"workload": f"Frenkel-Ladd switching, {replicas} x 8000-atom Si-cd (SW), 1000 K, k=5 eV/A^2",
             "atoms_per_replica": 8 * NCELL ** 3, "replicas_per_gpu": replicas,
             "md_steps_per_step": MD_STEPS, "dt_fs": 1.0, "switch_steps": NSCHED,
             "timed_window": "after the untimed equilibration and warm-up steps of the switching run",
-            "l2": "inputs larger than L2 (no flush)"}
+            "l2": "inputs larger than L2 (no flush)", "verlet_skin_A": skin}
 
 
 def peaks():
@@ -147,11 +147,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_context(N, replicas, precision, seed0=1000, stream=None):
+def build_context(N, replicas, precision, seed0=1000, stream=None, skin=None):
     from paper_2103_10449_gb300 import inputs as I
     x, box = I.diamond(NCELL, NCELL, NCELL)
     sv = math.sqrt(KB * T_SW / (MASS * MVV2E))
-    ctx = N.Context(precision=precision, dt=0.001, skin=SKIN, nbr_cap=48, stream=stream)
+    ctx = N.Context(precision=precision, dt=0.001, skin=SKIN if skin is None else skin, nbr_cap=48, stream=stream)
     for r in range(replicas):
         v = I.gaussian_velocities(len(x), sv, seed0 + r)
         s = ctx.add_system(x, box, v=v, r0=x, mass=MASS)
@@ -372,6 +372,7 @@ def main():
     ap.add_argument("--equil", type=int, default=3000,
                     help="untimed MD steps before warm-up (thermalises the crystals)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
+    ap.add_argument("--skin", type=float, default=SKIN, help="Verlet skin (A) of the timed context")
     ap.add_argument("--tuning", default=None,
                     help="pass A,pass B lanes per atom instead of autotuning (e.g. to profile a chosen configuration)")
     args = ap.parse_args()
@@ -398,7 +399,7 @@ def main():
     R = args.replicas
     stream = torch.cuda.Stream()
     from paper_2103_10449_gb300 import sharding as SH
-    ctx, natoms = build_context(N, R, N.NEFE_FP32, seed0=SH.rank_seed(1000, rank), stream=stream)
+    ctx, natoms = build_context(N, R, N.NEFE_FP32, seed0=SH.rank_seed(1000, rank), stream=stream, skin=args.skin)
     ctx.run(args.equil)
     if args.tuning:
         la, lb = (int(v) for v in args.tuning.split(","))
@@ -455,7 +456,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": workload_config(R), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+            "config": workload_config(R, args.skin), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
             "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild, "mean_shell": m_shell},
             "systems_with_errors": errors}
     del ctx

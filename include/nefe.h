@@ -332,9 +332,10 @@ NEFE_API int nefe_load(nefe_ctx* ctx, const char* path);
 
 /* Times the variants of both force passes on the current state and keeps the fastest:
  * pass A with 1 (one thread per atom), 4, 8, 16 or 32 lanes per atom (FP64: 8, 16, 32),
- * pass B with 1, 2, 4 or 8 lanes per atom (the list build keeps its lanes, 8 unless set).
- * Each kernel is first timed alone; then the two fastest pass-A variants with every pass-B
- * variant run as real steps on a device snapshot of the state, restored afterwards (the run
+ * pass B with 1, 2, 4 or 8 lanes per atom, the list build with 8, 16 or 32.  Each force pass
+ * is first timed alone; then the two fastest pass-A variants with every pass-B variant, and
+ * with the best pair each list-build variant, run as real steps on a device snapshot of the
+ * state, restored afterwards (the run
  * continues bit for bit as without the call; the snapshot needs about as much free device
  * memory as the state, and without it the kernel-level choice stands).  nefe_get_tuning
  * reports pass A's lanes and the time per MD step of the chosen pair (kernel-level: the two

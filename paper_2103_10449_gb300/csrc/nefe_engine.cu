@@ -900,6 +900,28 @@ static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>
             copy(false);
         }
     }
+    // then the list build's lanes with the chosen pair (its cost is only seen in real steps,
+    // where a few systems rebuild at a time)
+    int best_l = c->llanes;
+    for (int ll : {8, 16, 32}) {
+        if (rc != NEFE_OK || ll == best_l) continue;
+        c->lanes = best_a;
+        c->glanes = best_b;
+        c->llanes = ll;
+        c->b.list_lanes = ll;
+        drop_graph(c);
+        if ((rc = nefe_run(c, kGraphSteps))) break;
+        cudaEventRecord(e0, c->stream);
+        if ((rc = nefe_run(c, 2 * kGraphSteps))) break;
+        cudaEventRecord(e1, c->stream);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        const double us = 1000.0 * ms / (2 * kGraphSteps);
+        if (us < best) { best = us; best_l = ll; }
+        copy(false);
+    }
+    c->llanes = best_l;
+    c->b.list_lanes = best_l;
     cudaStreamSynchronize(c->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -981,8 +1003,8 @@ int nefe_autotune(nefe_ctx* c) {
         cudaFree(tv);
         cudaFree(tf);
     }
-    // the list build keeps its lanes: a full rebuild (the only thing timeable here) ranks the
-    // variants differently from the partial rebuilds of a run, where 8 lanes were measured best
+    // the list build's lanes are chosen in real steps only (refine_in_steps): a full rebuild,
+    // the only thing timeable here, ranks them differently from the partial rebuilds of a run
     const int best_ll = c->llanes;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
