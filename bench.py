@@ -300,6 +300,42 @@ def dcci_batched_throughput(N, torch, pairs=64, steps=5):
             "systems_with_errors": errors}
 
 
+def rs_npt_batched_throughput(N, torch, per_phase=20, steps=5):
+    """The reversible-scaling NPT workload: Si-cd (8000 atoms), beta-Sn (8192) and liquid (8000,
+    random positions at 2.53 g/cm^3) at 0 and 10 GPa, `per_phase` replicas of each phase and
+    pressure in one context (lambda 1 -> 0.2, i.e. 400 -> 2000 K, over 50000 steps; isotropic
+    barostat for cd and liquid, anisotropic for beta-Sn), FP32 kernels; atom-steps/s."""
+    from paper_2103_10449_gb300 import inputs as I
+    sv = math.sqrt(KB * 400.0 / (MASS * MVV2E))
+    stream = torch.cuda.Stream()
+    ctx = N.Context(precision=N.NEFE_FP32, dt=0.001, skin=SKIN, nbr_cap=48, stream=stream)
+    cd = I.diamond(10, 10, 10)
+    bt = I.beta_tin(8, 16, 16)
+    lq = I.liquid(8000, 0.05425, seed=4242)
+    natoms = 0
+    k = 0
+    for P in (0.0, 10.0):
+        for (x, box), baro in ((cd, N.NEFE_BARO_ISO), (bt, N.NEFE_BARO_ANISO), (lq, N.NEFE_BARO_ISO)):
+            for r in range(per_phase):
+                s = ctx.add_system(x, box, v=I.gaussian_velocities(len(x), sv, 6000 + k), mass=MASS)
+                ctx.set_thermostat(s, 400.0, 0.1, 6000 + k)
+                ctx.set_barostat(s, baro, P, 1.0)
+                ctx.set_schedule(s, N.NEFE_SCHED_RS, nsteps=50000, lambda_f=0.2, P_GPa=P)
+                natoms += len(x)
+                k += 1
+    ctx.setup()
+    ctx.run(320)
+    ctx.autotune()
+    ctx.run(2 * MD_STEPS)
+    ctx.sync()
+    wall = time_steps(torch, ctx, stream, steps, MD_STEPS)
+    errors = sum(1 for r in ctx.results_all() if r["error"] != 0)
+    ctx.close()
+    return {"workload": f"reversible scaling NPT, {per_phase} replicas each of 8000-atom Si-cd, 8192-atom beta-Sn "
+                        f"and 8000-atom liquid at 0 and 10 GPa (lambda 1 -> 0.2 over 50000 steps), FP32 kernels",
+            "atoms": natoms, "atom_steps_per_s": natoms * MD_STEPS * steps / wall, "systems_with_errors": errors}
+
+
 def time_steps(torch, ctx, stream, steps, md_steps):
     """Seconds for `steps` timed steps, from CUDA events on the context's stream."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -503,6 +539,7 @@ def main():
         line["dG_err"] = free_energy_error(N)
         line["differentiation"] = differentiation_throughput(N, torch)
         line["dcci_batched"] = dcci_batched_throughput(N, torch)
+        line["rs_npt_batched"] = rs_npt_batched_throughput(N, torch)
         cps, nst, dt = cpu_baseline_sample()
         line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{nst} FP64-oracle MD steps of one 8000-atom replica ({dt:.1f} s)"}
