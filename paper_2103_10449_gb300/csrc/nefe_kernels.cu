@@ -220,11 +220,15 @@ __device__ void cells_count_tile(const Bufs& b, int tile) {
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
     __shared__ int s_n3[3];
-    __shared__ double s_h[3];
+    __shared__ double s_h[3], s_ib[3];
     if (threadIdx.x == 0) {                      // the grid of this tile's system, once per tile
         int g3[3];
         const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, g3);
-        for (int k = 0; k < 3; ++k) { s_n3[k] = g3[k]; s_h[k] = __ddiv_rn(st.box[k], (double)g3[k]); }
+        for (int k = 0; k < 3; ++k) {
+            s_n3[k] = g3[k];
+            s_h[k] = __ddiv_rn(st.box[k], (double)g3[k]);
+            s_ib[k] = __ddiv_rn(1.0, st.box[k]);
+        }
         if (tile == S.tile0) {
             for (int k = 0; k < 3; ++k) { st.ncell[k] = g3[k]; st.h[k] = s_h[k]; st.hb[k] = s_h[k]; }
             refresh_box_f(st);
@@ -235,6 +239,12 @@ __device__ void cells_count_tile(const Bufs& b, int tile) {
     __syncthreads();
     const int n3[3] = {s_n3[0], s_n3[1], s_n3[2]};
     const double h[3] = {s_h[0], s_h[1], s_h[2]};
+    const double ib[3] = {s_ib[0], s_ib[1], s_ib[2]};
+    // The stateless cell sort reproduces the plain definition (x / L, correctly rounded); the
+    // engine's list build only needs a consistent cell for each atom (its cells are at least
+    // rcs (1 + 1e-9) wide and the list decision itself is exact), so it multiplies by 1/L
+    // instead of dividing (FP64 division is a long instruction sequence on this GPU).
+    const bool exact = b.rtiles == nullptr;
     __syncthreads();                             // the next tile of the loop rewrites the table
     if ((int)threadIdx.x >= ta.count) return;
     const int i = ta.first + threadIdx.x;
@@ -252,7 +262,7 @@ __device__ void cells_count_tile(const Bufs& b, int tile) {
             dh[k * N + i] = (T)0;
             if (b.dlo) dl[k * N + i] = (T)0;
         }
-        const double s = __ddiv_rn(xk, st.box[k]);
+        const double s = exact ? __ddiv_rn(xk, st.box[k]) : xk * ib[k];
         const double fl = floor(s);
         const double w = __dsub_rn(s, fl);
         int c = (int)__dmul_rn(w, (double)n3[k]);
@@ -1330,7 +1340,7 @@ __device__ void prepare_step(const DevSys& S, DevState& st, double dt) {
     bool scaled = false;
     for (int k = 0; k < 3; ++k) {
         const double z = st.eta[k] * dt;
-        st.s[k] = exp(z);
+        st.s[k] = (z != 0.0) ? exp(z) : 1.0;
         st.phi[k] = (z != 0.0) ? expm1(z) / z : 1.0;
         st.phi_f[k] = (float)st.phi[k];
         st.sm1_f[k] = (float)(st.s[k] - 1.0);
