@@ -478,7 +478,18 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     const T4* xc = reinterpret_cast<const T4*>(b.xcs) + S.off;
     if (lane == 0) cnt_s[grp] = 0;
     __syncwarp(gmask);
-    for (int o = lane; o < 27; o += L) {
+    // the lane's cells o = lane, lane + L, ...: every range is loaded first (independent
+    // loads in flight), then each range is walked VB candidates at a time (FP32: 4; FP64: 2,
+    // which keeps the wider positions in registers)
+    constexpr int KC = (27 + L - 1) / L;
+    constexpr int VB = sizeof(T) == 4 ? 4 : 2;
+    int lo_[KC], hi_[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int o = lane + k * L;
+        lo_[k] = 0;
+        hi_[k] = 0;
+        if (o >= 27) continue;
         const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
         const T ex = ox < 0 ? xi.x : (ox > 0 ? hx - xi.x : (T)0);
         const T ey = oy < 0 ? xi.y : (oy > 0 ? hy - xi.y : (T)0);
@@ -490,34 +501,47 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
         yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
         zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
         const int c2 = xx + nx * (yy + ny * zz);
-        const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
+        lo_[k] = start[c2];
+        hi_[k] = start[c2 + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int o = lane + k * L;
+        const int lo = max(0, min(lo_[k], S.n)), hi = max(lo, min(hi_[k], S.n));
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
         const T offx = (T)ox * hx, offy = (T)oy * hy, offz = (T)oz * hz;
-#pragma unroll 2
-        for (int p = lo; p < hi; ++p) {
-            const T4 xj = xc[p];
-            const int j = unpack_index(xj.w);
-            if (j < S.off || j >= S.off + S.n) {
-                atomicOr(&st.err, NEFE_ERR_CELL);
-                continue;
-            }
-            if (j == i && o == 13) continue;
-            const T dx = xj.x - xi.x + offx;
-            const T dy = xj.y - xi.y + offy;
-            const T dz = xj.z - xi.z + offz;
-            const T dd = dx * dx + dy * dy + dz * dz;
-            bool in = false;
-            if (dd < lo2) {
-                in = true;
-            } else if (dd <= hi2) {
-                double d[3];
-                in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
-                in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
-                     fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
-                     fabs(d[2] - (double)dz) < 0.5 * st.h[2];
-            }
-            if (in) {
-                const int pos = atomicAdd(&cnt_s[grp], 1);
-                if (pos < kMaxCap) buf[grp][pos] = j | (o << kCodeShift);
+        for (int p0 = lo; p0 < hi; p0 += VB) {
+            T4 xj[VB];
+#pragma unroll
+            for (int u = 0; u < VB; ++u)
+                if (p0 + u < hi) xj[u] = xc[p0 + u];
+#pragma unroll
+            for (int u = 0; u < VB; ++u) {
+                if (p0 + u >= hi) break;
+                const int j = unpack_index(xj[u].w);
+                if (j < S.off || j >= S.off + S.n) {
+                    atomicOr(&st.err, NEFE_ERR_CELL);
+                    continue;
+                }
+                if (j == i && o == 13) continue;
+                const T dx = xj[u].x - xi.x + offx;
+                const T dy = xj[u].y - xi.y + offy;
+                const T dz = xj[u].z - xi.z + offz;
+                const T dd = dx * dx + dy * dy + dz * dz;
+                bool in = false;
+                if (dd < lo2) {
+                    in = true;
+                } else if (dd <= hi2) {
+                    double d[3];
+                    in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
+                    in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
+                         fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
+                         fabs(d[2] - (double)dz) < 0.5 * st.h[2];
+                }
+                if (in) {
+                    const int pos = atomicAdd(&cnt_s[grp], 1);
+                    if (pos < kMaxCap) buf[grp][pos] = j | (o << kCodeShift);
+                }
             }
         }
     }
