@@ -206,6 +206,74 @@ def free_energy_error(N, reps=8, n_eq=500, n_sw=2000):
             "systems_with_errors": out["fp64"][2] + out["fp32"][2]}
 
 
+def precision_errors(N, reps=4, n_eq=2000, n_dcci=10000, n_rs=5000):
+    """FP32 against FP64 for the other results of the path, each from identical initial states
+    (equilibrated in FP64) with identical noise seeds in both precisions:
+    * the dCCI coexistence pressure: reps Si-cd (8000 atoms) / beta-Sn (8000 atoms) pairs in
+      temperature control from (400 K, 13.09 GPa) to 600 K over n_dcci steps, P_coex at the end;
+    * the reversible-scaling work: reps Si-cd replicas at 10 GPa, lambda 1 -> 0.5 over n_rs steps.
+    Returns each estimate per precision, their difference and the statistical error of the
+    FP64 estimate (standard error over the realisations)."""
+    from paper_2103_10449_gb300 import inputs as I
+    T0, P0, P_rs = 400.0, 13.09, 10.0
+    xa, ba = I.diamond(NCELL, NCELL, NCELL)
+    xb, bb = I.beta_tin(*I.beta_tin_cells_for(8000))
+    sv = math.sqrt(KB * T0 / (MASS * MVV2E))
+    eq = N.Context(precision=N.NEFE_FP64, dt=0.001, skin=SKIN, nbr_cap=48)
+    for r in range(reps):
+        for k, (x, b, mode) in enumerate(((xa, ba * 0.96, N.NEFE_BARO_ISO), (xb, bb, N.NEFE_BARO_ANISO))):
+            s = eq.add_system(x * (b[0] / (ba[0] if k == 0 else bb[0])), b,
+                              v=I.gaussian_velocities(len(x), sv, 8000 + 2 * r + k))
+            eq.set_thermostat(s, T0, 0.1, 8000 + 2 * r + k)
+            eq.set_barostat(s, mode, P0, 1.0)
+    for r in range(reps):
+        s = eq.add_system(xa * 0.98, ba * 0.98, v=I.gaussian_velocities(len(xa), sv, 8100 + r))
+        eq.set_thermostat(s, T0, 0.1, 8100 + r)
+        eq.set_barostat(s, N.NEFE_BARO_ISO, P_rs, 1.0)
+    eq.run(n_eq)
+    st = [eq.get_state(s) for s in range(3 * reps)]
+    eq.close()
+    out = {}
+    for name, prec in (("fp64", N.NEFE_FP64), ("fp32", N.NEFE_FP32)):
+        c = N.Context(precision=prec, dt=0.001, skin=SKIN, nbr_cap=48)
+        pids = []
+        for r in range(reps):
+            a = c.add_system(st[2 * r][0], st[2 * r][2], v=st[2 * r][1])
+            b = c.add_system(st[2 * r + 1][0], st[2 * r + 1][2], v=st[2 * r + 1][1])
+            c.set_thermostat(a, T0, 0.1, 8200 + 2 * r)
+            c.set_thermostat(b, T0, 0.1, 8201 + 2 * r)
+            c.set_barostat(a, N.NEFE_BARO_ISO, P0, 1.0)
+            c.set_barostat(b, N.NEFE_BARO_ANISO, P0, 1.0)
+            pids.append(c.pair_dcci(a, b, T0, P0, N.NEFE_DCCI_TEMP, T0, 600.0, n_dcci))
+        rs = []
+        for r in range(reps):
+            x, v, b = st[2 * reps + r]
+            s = c.add_system(x, b, v=v)
+            c.set_thermostat(s, T0, 0.1, 8300 + r)
+            c.set_barostat(s, N.NEFE_BARO_ISO, P_rs, 1.0)
+            c.set_schedule(s, N.NEFE_SCHED_RS, nsteps=n_rs, lambda_f=0.5, P_GPa=P_rs)
+            rs.append(s)
+        c.run(n_rs)
+        w = np.array([c.results(s)["W"] / len(xa) for s in rs])
+        c.run(n_dcci - n_rs)
+        pc = np.array([c.pair(p)[1] for p in pids])
+        errs = sum(int(r["error"] != 0) for r in c.results_all())
+        c.close()
+        out[name] = (pc, w, errs)
+    p64, w64, e64 = out["fp64"]
+    p32, w32, e32 = out["fp32"]
+    return {"dcci_P_coex": {"fp64_GPa": float(p64.mean()), "fp32_GPa": float(p32.mean()),
+                            "err_GPa": float(p32.mean() - p64.mean()),
+                            "stat_err_GPa": float(p64.std(ddof=1) / math.sqrt(reps)),
+                            "protocol": f"{reps} Si-cd/beta-Sn pairs (8000 + 8000 atoms), temperature control "
+                                        f"400 -> 600 K over {n_dcci} steps from 13.09 GPa"},
+            "rs_W": {"fp64_eV_per_atom": float(w64.mean()), "fp32_eV_per_atom": float(w32.mean()),
+                     "err_meV_per_atom": float(1000.0 * (w32.mean() - w64.mean())),
+                     "stat_err_meV_per_atom": float(1000.0 * w64.std(ddof=1) / math.sqrt(reps)),
+                     "protocol": f"{reps} Si-cd replicas (8000 atoms) at 10 GPa, lambda 1 -> 0.5 over {n_rs} steps"},
+            "systems_with_errors": e64 + e32}
+
+
 def differentiation_throughput(N, torch):
     """The differentiation workload: (i) the SW energy + forces + seven parameter derivatives
     (nefe_sw_energy_grad, the backward of the autograd.Function) on diamond cells from 8000 to
@@ -537,6 +605,7 @@ def main():
         comp["batched_fp32_over_fp64_batched"] = value / world / comp["fp64_batched"]
         line["comparators"] = comp
         line["dG_err"] = free_energy_error(N)
+        line["precision_errors"] = precision_errors(N)
         line["differentiation"] = differentiation_throughput(N, torch)
         line["dcci_batched"] = dcci_batched_throughput(N, torch)
         line["rs_npt_batched"] = rs_npt_batched_throughput(N, torch)
