@@ -28,8 +28,10 @@ paper"); every one is repeated in the docstring of the routine that implements i
 Parity status: the SW energy/forces, neighbour list, cells, Philox, Einstein free energy,
 integrator, thermostat, schedules, estimators and dCCI algebra are pinned by tests in
 ``tests/test_oracle_pins.py``.  The barostat equation is a reading (the paper names
-Parrinello-Rahman but gives no equations): parity unpinned against the paper; it is pinned
-only by its own invariants (volume response sign, hydrostatic equilibrium).
+Parrinello-Rahman but gives no equations).  Its equilibrium is pinned by a closed form:
+pressure switching of an ideal gas reproduces (N - 1) kB T ln(P1/P0), and its invariants
+(volume response sign, hydrostatic equilibrium) are tested.  Its dynamics (the box mass and
+the form of the box equation) remain unpinned against the paper.
 """
 from __future__ import annotations
 

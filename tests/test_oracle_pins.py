@@ -400,6 +400,45 @@ def test_barostat_restores_target_pressure():
     assert abs(np.mean(P)) * O.EV_A3_TO_GPA < 0.3         # GPa, fluctuations ~1 GPa at 64 atoms
 
 
+def _ideal_gas_as_work(n, seed, p_from, p_to, nsched, n_eq, T):
+    """Work of one pressure switch p_from -> p_to of n non-interacting atoms (U = 0) after
+    n_eq steps of NPT equilibration at p_from; pressures in eV/A^3."""
+    kT = O.KB * T
+    L = ((n - 1) * kT / p_from) ** (1.0 / 3.0)
+    x = np.random.default_rng(seed).uniform(0.0, L, (n, 3))
+    common = dict(pot=O.POT_EINSTEIN, k_int=0.0, T=T, tdamp=0.1, sys_id=0, baro=O.BARO_ISO, p_ext=p_from,
+                  pdamp=0.5)
+    eq = O.System(x=x, v=I.gaussian_velocities(n, _sv(T), seed), box=np.array([L, L, L]), r0=x.copy(), seed=seed,
+                  **common)
+    eq.run(n_eq)
+    sw = O.System(x=eq.x.copy(), v=eq.v.copy(), box=eq.box.copy(), r0=eq.x.copy(), seed=seed + 1000,
+                  sched=O.SCHED_AS, nsched=nsched, p0=p_from, p1=p_to, **common)
+    sw.eta = eq.eta.copy()
+    sw.run(nsched)
+    return sw.W
+
+
+def test_pressure_switching_of_an_ideal_gas_closed_form():
+    """Adiabatic switching in pressure (Sec. 2.3, Eq. Gibbs_AS) of an ideal gas, 16 atoms at
+    400 K, 0.1 -> 0.3 GPa and back, 8 + 8 realisations of 10 ps.  With U = 0 the virial vanishes,
+    so P_inst V = 2K/3.  The box equation is stationary only if <V (P_inst - P)> = 0, and the
+    thermostat, which removes the net momentum, leaves 3N - 3 degrees of freedom: <2K/3> =
+    (N - 1) kB T.  Hence <V>(P) = (N - 1) kB T / P and the reversible work is
+    dG = (N - 1) kB T ln(P1 / P0), the ideal gas's Gibbs energy change with N - 1 for N.
+    This pins the switching work (left-point sum of V dP, pressure units, sign), the estimator
+    and the barostat's mechanical equilibrium; a 3N-degree count would be off by 1/16 = 6 %."""
+    n, T = 16, 400.0
+    p0, p1 = 0.1 / O.EV_A3_TO_GPA, 0.3 / O.EV_A3_TO_GPA
+    reps, nsched, n_eq = 8, 10000, 2000
+    wf = np.array([_ideal_gas_as_work(n, 10 + r, p0, p1, nsched, n_eq, T) for r in range(reps)])
+    wb = np.array([_ideal_gas_as_work(n, 40 + r, p1, p0, nsched, n_eq, T) for r in range(reps)])
+    dG = float(O.gibbs_as(0.0, wf.mean(), wb.mean()))
+    exact = (n - 1) * O.KB * T * math.log(p1 / p0)
+    sem = 0.5 * math.sqrt(wf.var(ddof=1) / reps + wb.var(ddof=1) / reps)
+    assert sem < 0.01 * exact
+    assert abs(dG / exact - 1.0) < 0.03          # about four standard errors
+
+
 def test_dcci_pair_replays_the_discrete_equations():
     """The pair update uses the instantaneous per-atom dU, dV of both systems each step and
     is the composition of Eq. Ps_coex_discreted / Eq. l_coex_discreted step by step."""
