@@ -439,6 +439,44 @@ def test_pressure_switching_of_an_ideal_gas_closed_form():
     assert abs(dG / exact - 1.0) < 0.03          # about four standard errors
 
 
+def _ideal_gas_rs_work(n, seed, P, lam_f, direction, nsched, n_eq, T):
+    """Work of one reversible-scaling switch (NPT, physical pressure P in eV/A^3) of n
+    non-interacting atoms, after n_eq steps of equilibration at the starting lambda (1
+    forward, lam_f backward), where the barostat target is lambda P."""
+    kT = O.KB * T
+    lam0 = 1.0 if direction > 0 else lam_f
+    L = ((n - 1) * kT / (lam0 * P)) ** (1.0 / 3.0)
+    x = np.random.default_rng(seed).uniform(0.0, L, (n, 3))
+    common = dict(pot=O.POT_EINSTEIN, k_int=0.0, T=T, tdamp=0.1, sys_id=0, baro=O.BARO_ISO, pdamp=0.5)
+    eq = O.System(x=x, v=I.gaussian_velocities(n, _sv(T), seed), box=np.array([L, L, L]), r0=x.copy(), seed=seed,
+                  p_ext=lam0 * P, **common)
+    eq.run(n_eq)
+    sw = O.System(x=eq.x.copy(), v=eq.v.copy(), box=eq.box.copy(), r0=eq.x.copy(), seed=seed + 1000, p_ext=P,
+                  sched=O.SCHED_RS, direction=direction, nsched=nsched, lam_f=lam_f, **common)
+    sw.eta = eq.eta.copy()
+    sw.run(nsched)
+    return sw.W
+
+
+def test_reversible_scaling_npt_of_an_ideal_gas_closed_form():
+    """Reversible scaling at constant pressure (Sec. 2.2, Eq. dH_RS with P_S = lambda P, the
+    barostat target of the ``ners`` tag) of an ideal gas, 16 atoms, T0 = 400 K, P = 0.1 GPa,
+    lambda 1 -> 0.5 and back, 8 + 8 realisations of 10 ps.  With U = 0 the driving force is
+    P V, and at target lambda P the box settles at <V> = (N - 1) kB T0 / (lambda P) (as in the
+    pressure-switching pin), so the reversible work is the integral of (N - 1) kB T0 / lambda,
+    i.e. (N - 1) kB T0 ln(lambda_f).  Together with the kinetic term of Eq. Gibbs_RS this is the
+    ideal gas's G(T) = (T/T0) G(T0) - 5/2 N kB T ln(T/T0), up to the N - 1 degrees count."""
+    n, T0, P, lam_f = 16, 400.0, 0.1 / O.EV_A3_TO_GPA, 0.5
+    reps, nsched, n_eq = 8, 10000, 2000
+    wf = np.array([_ideal_gas_rs_work(n, 10 + r, P, lam_f, 1, nsched, n_eq, T0) for r in range(reps)])
+    wb = np.array([_ideal_gas_rs_work(n, 40 + r, P, lam_f, -1, nsched, n_eq, T0) for r in range(reps)])
+    w_rev = 0.5 * (wf.mean() - wb.mean())
+    exact = (n - 1) * O.KB * T0 * math.log(lam_f)
+    sem = 0.5 * math.sqrt(wf.var(ddof=1) / reps + wb.var(ddof=1) / reps)
+    assert sem < 0.01 * abs(exact)
+    assert abs(w_rev / exact - 1.0) < 0.03        # about four standard errors
+
+
 def test_dcci_pair_replays_the_discrete_equations():
     """The pair update uses the instantaneous per-atom dU, dV of both systems each step and
     is the composition of Eq. Ps_coex_discreted / Eq. l_coex_discreted step by step."""
