@@ -974,13 +974,20 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     auto get_u = [&](int a) -> T4 { return a < K1 ? sh_u[a][t] : spu[a - K1]; };
     auto put_r = [&](int a, T v) { if (a < K1) sh_r[a][t] = v; else spr[a - K1] = v; };
     auto get_r = [&](int a) -> T { return a < K1 ? sh_r[a][t] : spr[a - K1]; };
-    // 1. compaction, four row entries in flight
+    // 1. compaction, four row entries in flight (one 16-byte load of the row when its rows are
+    // 16-byte aligned, i.e. the row capacity is a multiple of 4; entries past ci are not used)
     int m = 0;
+    const bool row4 = (b.cap & 3) == 0;
     for (int base = 0; base < ci; base += 4) {
         int e[4];
         T4 xj[4];
+        if (row4) {
+            const int4 r4 = *reinterpret_cast<const int4*>(row + base);
+            e[0] = r4.x; e[1] = r4.y; e[2] = r4.z; e[3] = r4.w;
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = (base + u < ci) ? row[base + u] : 0;
+            for (int u = 0; u < 4; ++u) e[u] = (base + u < ci) ? row[base + u] : 0;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (base + u < ci) xj[u] = reinterpret_cast<const T4*>(b.xs)[e[u] & (int)kIndexMask];
@@ -1131,10 +1138,16 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
             for (int base = 0; base < m; base += NB * L) {
                 int jj[NB], pos[NB];
                 int4 q0[NB], q1[NB];
+                if constexpr (NB == 2 && L == 1) {   // both entries with one 8-byte load (rows are 128 bytes)
+                    const int2 j2 = *reinterpret_cast<const int2*>(b.shj + (size_t)i * kShell + base);
+                    jj[0] = j2.x;
+                    jj[NB - 1] = base + 1 < m ? j2.y : -1;
+                } else {
 #pragma unroll
-                for (int u = 0; u < NB; ++u) {
-                    const int a = base + u * L + lane;
-                    jj[u] = a < m ? b.shj[(size_t)i * kShell + a] : -1;
+                    for (int u = 0; u < NB; ++u) {
+                        const int a = base + u * L + lane;
+                        jj[u] = a < m ? b.shj[(size_t)i * kShell + a] : -1;
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < NB; ++u) {
