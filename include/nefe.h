@@ -269,24 +269,43 @@ typedef struct nefe_results {
 
 /*
  * nefe_create - new context on CUDA device `device`, issuing work on `stream` (cudaStream_t
- * as void*, NULL = a stream the context creates).  precision: NEFE_FP32 / NEFE_FP64.
- * dt_ps: time step (the paper uses 1 fs = 0.001 ps).  skin: list skin (A).
- * nbr_cap: neighbour row capacity (16..64).
+ * as void*, NULL = a stream the context creates).  A context holds every simulated cell of a
+ * study (replicas, both phases of each dCCI pair; Sec. 4 runs 10 realisations per estimate and
+ * two coupled partitions for dCCI) and advances them together.  precision: NEFE_FP32 /
+ * NEFE_FP64.  dt_ps: time step (Sec. 4 uses 1 fs = 0.001 ps).  skin: list skin (A).
+ * nbr_cap: neighbour row capacity (16..64).  NEFE_EINVAL on bad arguments, NEFE_ECUDA when no
+ * device is usable.  The context owns all its device memory (released by nefe_destroy).
  */
 NEFE_API int nefe_create(nefe_ctx** out, int device, void* stream, int precision, double dt_ps,
                 double skin, int nbr_cap);
 NEFE_API int nefe_destroy(nefe_ctx* ctx);
+/* Message of the most recent failure on the calling thread, whatever context or call it came
+ * from (the library keeps one message per thread, not per context). */
 NEFE_API const char* nefe_last_error(void);
 
-/* Adds a system before the first nefe_run; *sys_id receives its index (0, 1, ...). */
+/* Adds a system (one periodic cell of Sec. 4: Si-cd, beta-Sn or liquid) before the first
+ * nefe_run; *sys_id receives its index (0, 1, ...).  The host arrays of desc are copied.
+ * NEFE_EINVAL on n < 2, NULL x or a non-positive box; NEFE_ESTATE after setup. */
 NEFE_API int nefe_add_system(nefe_ctx* ctx, const nefe_system_desc* desc, int* sys_id);
 /* Potential parameters for one system, or all systems when sys == -1. */
 NEFE_API int nefe_set_sw_params(nefe_ctx* ctx, int sys, const nefe_sw_params* prm);
 /* Langevin thermostat: T (K), damping time (ps; <= 0 switches it off), noise seed.
  * The random force of each step has its per-system mean removed ("zero yes", Sec. 4). */
 NEFE_API int nefe_set_thermostat(nefe_ctx* ctx, int sys, double T, double damp_ps, uint64_t seed);
-/* Box equation: mode NEFE_BARO_*, target pressure (GPa), damping time (ps). */
+/* Box equation (Sec. 4: "Parrinello-Rahman", LAMMPS fix nph iso for Si-cd and the liquid, aniso for
+ * beta-Sn, with the "ners" tag that multiplies the target by lambda in reversible scaling):
+ * mode NEFE_BARO_*, target pressure (GPa; the physical P of an RS schedule is set there
+ * instead), damping time tau_P (ps): box mass Q_b = (N + 1) kB T tau_P^2.  The box equation is
+ * a reading (the paper prints none): eta' = d V (P - P_target) / Q_b with d = 3 (iso, one
+ * strain rate) or d = 1 per axis driven by P_aa (aniso), affine drift of the positions.
+ * NEFE_EINVAL on a bad mode or pdamp <= 0; NEFE_ESTATE after setup. */
 NEFE_API int nefe_set_barostat(nefe_ctx* ctx, int sys, int mode, double P_GPa, double pdamp_ps);
+/* Switching path of one system (NEFE_SCHED_*): Hamiltonian interpolation to the Einstein crystal
+ * (Sec. 2.1, Eqs. H_lambda, Wrev_HI), reversible scaling (Sec. 2.2, Eqs. H_RS, dH_RS, with the
+ * Sec. 4 lambda variable), pressure switching (Sec. 2.3, Eqs. Wmech, Wmech_dyn), or a fixed
+ * lambda.  The work W = sum_k dH/dlambda (lambda_{k+1} - lambda_k) (Eq. Wdyn, left point) is
+ * accumulated in FP64 on the device.  NEFE_EINVAL on an unknown kind or nsteps < 1;
+ * NEFE_ESTATE after setup. */
 NEFE_API int nefe_set_schedule(nefe_ctx* ctx, int sys, const nefe_schedule* sched);
 /*
  * nefe_pair_dcci - couples systems sysI and sysII (phase I, phase II) through the dCCI
@@ -312,7 +331,11 @@ NEFE_API int nefe_run(nefe_ctx* ctx, long nsteps);
 /* Blocks until the context's stream is idle; returns NEFE_ECUDA on an asynchronous error. */
 NEFE_API int nefe_sync(nefe_ctx* ctx);
 
-/* Blocking reads (they synchronise the stream first). */
+/* Blocking reads (they synchronise the stream first).  nefe_get_results: the dynamical work W
+ * of Eq. Wdyn (left point; forward and backward runs give Eqs. dF and Qdiss on the host),
+ * the instantaneous and mean H, dH/dlambda, P and V of the system (Sec. 2), lambda and the
+ * error word; NEFE_EINVAL for an unknown system.  nefe_get_pair: T_coex = T0 / lambda and
+ * P_coex = P_S / lambda of a dCCI pair (Sec. 3, Eqs. T_sc, P_sc). */
 NEFE_API int nefe_get_results(nefe_ctx* ctx, int sys, nefe_results* out);
 NEFE_API int nefe_get_pair(nefe_ctx* ctx, int pair, double* T_coex, double* P_coex_GPa,
                   double* lambda, unsigned* error);

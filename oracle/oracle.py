@@ -22,16 +22,19 @@ this module wraps them with ctypes and writes out, step by step, what the paper 
   Parrinello-Rahman-type box equation whose target pressure is multiplied by lambda
   (Sec. 4: "Langevin thermostat", "velocity-Verlet", dt = 1 fs, the ``ners`` tag).
 
-Where the paper is silent the readings are the ones listed in DESIGN.md ("Readings of the
-paper"); every one is repeated in the docstring of the routine that implements it.
+Where the paper is silent, the reading taken is stated in the docstring of the routine
+that implements it.
 
 Parity status: the SW energy/forces, neighbour list, cells, Philox, Einstein free energy,
-integrator, thermostat, schedules, estimators and dCCI algebra are pinned by tests in
-``tests/test_oracle_pins.py``.  The barostat equation is a reading (the paper names
-Parrinello-Rahman but gives no equations).  Its equilibrium is pinned by a closed form:
-pressure switching of an ideal gas reproduces (N - 1) kB T ln(P1/P0), and its invariants
-(volume response sign, hydrostatic equilibrium) are tested.  Its dynamics (the box mass and
-the form of the box equation) remain unpinned against the paper.
+integrator, thermostat, schedules, estimators (including the sign of Eq. dA) and the dCCI
+updates (against the exact Clausius-Clapeyron line for constant dU, dV) are pinned by tests
+in ``tests/test_oracle_pins.py``.  The barostat equation is a reading (the paper names
+Parrinello-Rahman but gives no equations).  Its equilibrium is pinned by closed forms:
+pressure switching of an ideal gas reproduces (N - 1) kB T ln(P1/P0) for the isotropic and
+the anisotropic form, and the anisotropic form relaxes each axis of a beta-Sn cell to the
+static enthalpy minimum.  Its dynamics are pinned to the reading (the small-oscillation
+frequency of the volume of an ideal gas); that reading itself has no counterpart in the
+paper.
 """
 from __future__ import annotations
 

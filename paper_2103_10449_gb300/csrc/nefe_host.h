@@ -26,7 +26,10 @@ int cuda_fail(cudaError_t e, const char* where);
 inline bool host_grid(const double box[3], double rcs, int n3[3]) {
     bool ok = true;
     for (int k = 0; k < 3; ++k) {
-        int m = (int)std::floor(box[k] / rcs);
+        // clamped before the conversion to int (a huge box would overflow it); so many cells
+        // exceed every capacity and are rejected by the callers' cell-count check
+        const double q = std::floor(box[k] / rcs);
+        int m = q < (double)(1 << 20) ? (int)q : (1 << 20);
         while (m > 0 && box[k] / (double)m < rcs * (1.0 + 1e-9)) --m;
         if (m < 2) ok = false;
         n3[k] = m < 2 ? 2 : m;

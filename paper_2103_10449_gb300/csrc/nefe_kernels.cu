@@ -111,9 +111,13 @@ template <> struct Noise<float> {
 };
 
 // ------------------------------------------------------------------------------------
-// Deterministic per-system sums: warp shuffle in kernel precision -> FP64 across warps ->
-// one int64 fixed-point atomic per value into slot (blockIdx % kSlots).  Every thread of
-// the block must call it.
+// Deterministic per-system sums: warp shuffle in kernel precision, then the block's warp
+// partials summed in kernel precision in a fixed order, then one int64 fixed-point atomic per
+// value into slot (blockIdx % kSlots).  The FP64 path converts the block sum at 2^-32; the
+// FP32 path rounds it to a multiple of 2^-16 (an int32 conversion, |block sum| < 32768) before
+// moving it to the 2^-32 scale, so a block's contribution carries at most 2^-17 of rounding
+// on top of its FP32 summation error.  Integer addition makes the per-system total independent
+// of the order in which blocks arrive.  Every thread of the block must call it.
 // ------------------------------------------------------------------------------------
 template <typename T, int K>
 __device__ __forceinline__ void block_sum_to_acc(T (&v)[K], long long* acc_sys, int first,

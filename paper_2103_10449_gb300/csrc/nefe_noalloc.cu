@@ -55,6 +55,21 @@ int scratch_address(void** out) {
     return NEFE_OK;
 }
 
+// Writes the one-system descriptors (passed by value, so the call issues no host-to-device
+// copy from host memory), the tile table (every tile belongs to system 0) and zeroed
+// occupancy counts into the scratch.
+__global__ void k_noalloc_init(DevSys hs, DevState st, DevSys* dsys, DevState* dst, int* tile_sys, int ntiles,
+                               int* counts, int ncells) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    if (t == 0) {
+        *dsys = hs;
+        *dst = st;
+    }
+    for (int i = t; i < ntiles; i += stride) tile_sys[i] = 0;
+    for (int i = t; i < ncells; i += stride) counts[i] = 0;
+}
+
 }  // namespace
 }  // namespace nefe
 
@@ -68,9 +83,8 @@ extern "C" int nefe_cell_bin_noalloc(const double* x, int n, const double box[3]
     if (n > NEFE_NOALLOC_MAX_ATOMS)
         return fail(NEFE_EINVAL, "nefe_cell_bin_noalloc: n = %d above the fixed maximum of %d atoms", n,
                     NEFE_NOALLOC_MAX_ATOMS);
-    for (int k = 0; k < 3; ++k)
-        if (!(box[k] > 0.0) || !(box[k] >= 2.0 * rcs) || !(rcs > 0.0))
-            return fail(NEFE_EINVAL, "nefe_cell_bin_noalloc: box length below 2*rcs or rcs not positive");
+    int rc = check_box(box, rcs);
+    if (rc) return rc;
     int n3[3];
     if (!host_grid(box, rcs, n3)) return fail(NEFE_EINVAL, "nefe_cell_bin_noalloc: fewer than 2 cells on an axis");
     const long long total = (long long)n3[0] * n3[1] * n3[2];
@@ -85,7 +99,7 @@ extern "C" int nefe_cell_bin_noalloc(const double* x, int n, const double box[3]
         return NEFE_OK;
     }
     void* base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     unsigned char* p = static_cast<unsigned char*>(base);
     const int ntiles = (n + kTile - 1) / kTile;
@@ -98,11 +112,16 @@ extern "C" int nefe_cell_bin_noalloc(const double* x, int n, const double box[3]
     std::memset(&st, 0, sizeof(st));
     for (int k = 0; k < 3; ++k) st.box[k] = box[k];
     st.rebuild = 1;
-    // descriptors, tile table (all tiles belong to system 0) and zeroed occupancy counts
-    NEFE_CU(cudaMemcpyAsync(p + kOffSys, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
-    NEFE_CU(cudaMemcpyAsync(p + kOffSt, &st, sizeof(st), cudaMemcpyHostToDevice, s));
-    NEFE_CU(cudaMemsetAsync(p + kOffTile, 0, sizeof(int) * (size_t)ntiles, s));
-    NEFE_CU(cudaMemsetAsync(p + kOffCount, 0, sizeof(int) * (size_t)total, s));
+    // descriptors, tile table and zeroed occupancy counts, all written by one kernel
+    {
+        const int work = ntiles > (int)total ? ntiles : (int)total;
+        const int blocks = (work + 255) / 256 < 152 ? (work + 255) / 256 : 152;
+        k_noalloc_init<<<blocks, 256, 0, s>>>(hs, st, reinterpret_cast<DevSys*>(p + kOffSys),
+                                               reinterpret_cast<DevState*>(p + kOffSt),
+                                               reinterpret_cast<int*>(p + kOffTile), ntiles,
+                                               reinterpret_cast<int*>(p + kOffCount), (int)total);
+        NEFE_CU(cudaGetLastError());
+    }
 
     Bufs b;
     std::memset(&b, 0, sizeof(b));

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
 
-Tolerances (see DESIGN.md "Tolerances"): neighbour lists and cells bit-exact; SW energy,
+Tolerances: neighbour lists and cells bit-exact; SW energy,
 forces and virial within 1e-10 (FP64 kernel) or 1e-5 (FP32 kernel) relative, forces measured
 normwise as max|dF| / max|F|; thermostat noise from the same Philox stream within 1e-14
 (FP64 transform) / 2e-4 (FP32 transform on 24-bit uniforms, whose rounding the Box-Muller
@@ -239,7 +239,7 @@ def test_run_is_bitwise_deterministic(N):
 
 
 def test_thread_per_atom_pass_a_with_spilled_shells(N):
-    """A random liquid has in-cutoff shells beyond the 12 entries the one-thread-per-atom pass A
+    """A random liquid has in-cutoff shells beyond the 8 entries the one-thread-per-atom pass A
     keeps in shared memory; the rest live in its global spill area.  Ten FP32 steps against the
     FP64 oracle (NVT, 1700 K)."""
     x0, box = I.liquid(512, 0.05425, seed=81)
@@ -256,7 +256,7 @@ def test_thread_per_atom_pass_a_with_spilled_shells(N):
     res = ctx.results(s)
     x, v, _ = ctx.get_state(s)
     ctx.close()
-    assert mx > 12
+    assert mx > 8
     assert res["error"] == 0
     assert np.abs(x - orc.x).max() < 1e-4
     assert res["U"] == pytest.approx(orc.results()["U"], rel=1e-5)

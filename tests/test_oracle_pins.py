@@ -340,6 +340,10 @@ def test_harmonic_switching_reproduces_closed_form():
     exact = 1.5 * O.KB * T * math.log(10.0 / 5.0)
     assert abs(dF - exact) < 1e-3                          # 1 meV/atom
     assert 0.0 < O.dissipated_heat(wf, wb) / n < 5e-3      # second law: dissipation >= 0
+    # Eq. dA: the system at lambda = 0 (spring 5) from the reference at lambda = 1 (spring 10).
+    # A sign error (F_ref + dF) would miss the closed form by 2 dF = 72 meV/atom.
+    f_int = O.helmholtz_from_switching(O.einstein_free_energy(n, 10.0, T), wf, wb)
+    assert abs(f_int - O.einstein_free_energy(n, 5.0, T)) / n < 1e-3
 
 
 def test_langevin_equipartition_harmonic():
@@ -400,15 +404,17 @@ def test_barostat_restores_target_pressure():
     assert abs(np.mean(P)) * O.EV_A3_TO_GPA < 0.3         # GPa, fluctuations ~1 GPa at 64 atoms
 
 
-def _ideal_gas_as_work(n, seed, p_from, p_to, nsched, n_eq, T):
+def _ideal_gas_as_work(n, seed, p_from, p_to, nsched, n_eq, T, baro=O.BARO_ISO, shape=(1.0, 1.0, 1.0)):
     """Work of one pressure switch p_from -> p_to of n non-interacting atoms (U = 0) after
-    n_eq steps of NPT equilibration at p_from; pressures in eV/A^3."""
+    n_eq steps of NPT equilibration at p_from; pressures in eV/A^3.  ``shape`` gives the box
+    edge ratios (a tetragonal box for the anisotropic box equation)."""
     kT = O.KB * T
-    L = ((n - 1) * kT / p_from) ** (1.0 / 3.0)
-    x = np.random.default_rng(seed).uniform(0.0, L, (n, 3))
-    common = dict(pot=O.POT_EINSTEIN, k_int=0.0, T=T, tdamp=0.1, sys_id=0, baro=O.BARO_ISO, p_ext=p_from,
+    L = ((n - 1) * kT / p_from / np.prod(shape)) ** (1.0 / 3.0)
+    box = L * np.asarray(shape, dtype=np.float64)
+    x = np.random.default_rng(seed).uniform(0.0, 1.0, (n, 3)) * box
+    common = dict(pot=O.POT_EINSTEIN, k_int=0.0, T=T, tdamp=0.1, sys_id=0, baro=baro, p_ext=p_from,
                   pdamp=0.5)
-    eq = O.System(x=x, v=I.gaussian_velocities(n, _sv(T), seed), box=np.array([L, L, L]), r0=x.copy(), seed=seed,
+    eq = O.System(x=x, v=I.gaussian_velocities(n, _sv(T), seed), box=box, r0=x.copy(), seed=seed,
                   **common)
     eq.run(n_eq)
     sw = O.System(x=eq.x.copy(), v=eq.v.copy(), box=eq.box.copy(), r0=eq.x.copy(), seed=seed + 1000,
@@ -418,7 +424,8 @@ def _ideal_gas_as_work(n, seed, p_from, p_to, nsched, n_eq, T):
     return sw.W
 
 
-def test_pressure_switching_of_an_ideal_gas_closed_form():
+@pytest.mark.parametrize("baro,shape", [(O.BARO_ISO, (1.0, 1.0, 1.0)), (O.BARO_ANISO, (1.0, 1.0, 0.6))])
+def test_pressure_switching_of_an_ideal_gas_closed_form(baro, shape):
     """Adiabatic switching in pressure (Sec. 2.3, Eq. Gibbs_AS) of an ideal gas, 16 atoms at
     400 K, 0.1 -> 0.3 GPa and back, 8 + 8 realisations of 10 ps.  With U = 0 the virial vanishes,
     so P_inst V = 2K/3.  The box equation is stationary only if <V (P_inst - P)> = 0, and the
@@ -426,12 +433,16 @@ def test_pressure_switching_of_an_ideal_gas_closed_form():
     (N - 1) kB T.  Hence <V>(P) = (N - 1) kB T / P and the reversible work is
     dG = (N - 1) kB T ln(P1 / P0), the ideal gas's Gibbs energy change with N - 1 for N.
     This pins the switching work (left-point sum of V dP, pressure units, sign), the estimator
-    and the barostat's mechanical equilibrium; a 3N-degree count would be off by 1/16 = 6 %."""
+    and the barostat's mechanical equilibrium; a 3N-degree count would be off by 1/16 = 6 %.
+    The anisotropic box equation (one strain rate per axis, driven by P_aa) runs the same
+    switch in a tetragonal box: each axis is stationary only at <V (P_aa - P)> = 0, and for
+    the ideal gas every P_aa V is 2 K_a with K_a the kinetic energy of that axis (N - 1 degrees
+    of freedom each), which gives the same closed form."""
     n, T = 16, 400.0
     p0, p1 = 0.1 / O.EV_A3_TO_GPA, 0.3 / O.EV_A3_TO_GPA
     reps, nsched, n_eq = 8, 10000, 2000
-    wf = np.array([_ideal_gas_as_work(n, 10 + r, p0, p1, nsched, n_eq, T) for r in range(reps)])
-    wb = np.array([_ideal_gas_as_work(n, 40 + r, p1, p0, nsched, n_eq, T) for r in range(reps)])
+    wf = np.array([_ideal_gas_as_work(n, 10 + r, p0, p1, nsched, n_eq, T, baro, shape) for r in range(reps)])
+    wb = np.array([_ideal_gas_as_work(n, 40 + r, p1, p0, nsched, n_eq, T, baro, shape) for r in range(reps)])
     dG = float(O.gibbs_as(0.0, wf.mean(), wb.mean()))
     exact = (n - 1) * O.KB * T * math.log(p1 / p0)
     sem = 0.5 * math.sqrt(wf.var(ddof=1) / reps + wb.var(ddof=1) / reps)
@@ -501,3 +512,122 @@ def test_dcci_pair_replays_the_discrete_equations():
         assert pair.error == 0
         T_c, P_c = pair.coexistence()
         assert T_c == pytest.approx(400.0 / pair.lam) and P_c == pytest.approx(pair.ps / pair.lam)
+
+
+def test_anisotropic_box_equation_relaxes_each_axis_to_the_enthalpy_minimum():
+    """The anisotropic box equation (the beta-Sn barostat of Sec. 4, ``nph aniso``) drives
+    each axis by its own P_aa.  A 64-atom beta-Sn cell (A5 has no internal coordinate) started
+    at c/a = 0.55 and run at 300 K and 10 GPa must relax to the lattice constants that minimise the
+    static enthalpy E(a, b, c) + P a b c (found here by scipy over all three edges, thermal
+    expansion at 300 K is below 1 %), and every diagonal pressure component must average to
+    the target separately.  Driving all axes by the mean pressure would keep c/a at 0.55,
+    4 % from the minimum, with P_zz and P_xx apart by several GPa."""
+    from scipy.optimize import minimize
+    P, T = 10.0 / O.EV_A3_TO_GPA, 300.0
+    x1, b1 = I.beta_tin(2, 2, 4, a=1.0, c_over_a=1.0)
+
+    def enthalpy(edges):
+        e = O.sw_energy(x1 * (np.asarray(edges) / b1), np.asarray(edges))[0]
+        return e + P * float(np.prod(edges))
+    x0, box0 = I.beta_tin(2, 2, 4)
+    opt = minimize(enthalpy, box0, method="Nelder-Mead", options=dict(xatol=1e-8, fatol=1e-12, maxiter=4000))
+    s = O.System(x=x0.copy(), v=I.gaussian_velocities(len(x0), _sv(T), 3), box=box0.copy(), T=T, tdamp=0.1,
+                 seed=3, baro=O.BARO_ANISO, p_ext=P, pdamp=0.5)
+    s.run(3000)
+    B, VP, V = [], [], []
+    for k in range(6000):
+        s.step()
+        if k % 5 == 0:
+            Vk, Pt = s.observe()[:2]
+            B.append(s.box.copy())
+            VP.append(Vk * Pt[:3])
+            V.append(Vk)
+    box = np.mean(B, axis=0)
+    assert np.abs(box / opt.x - 1.0).max() < 0.01
+    assert abs((box[2] / box[0]) / (opt.x[2] / opt.x[0]) - 1.0) < 0.01
+    p_axes = np.mean(VP, axis=0) / np.mean(V) * O.EV_A3_TO_GPA
+    assert np.abs(p_axes - 10.0).max() < 0.1                     # GPa, each axis separately
+
+
+@pytest.mark.parametrize("baro,omega_tau", [(O.BARO_ISO, 3.0), (O.BARO_ANISO, math.sqrt(3.0))])
+def test_box_equation_small_oscillation_frequency(baro, omega_tau):
+    """Dynamics of the box equation (the reading: eta' = d V (P - P_target) / Q_b with
+    Q_b = (N + 1) kB T tau_P^2, d = 3 for the isotropic form, d = 1 per axis for the anisotropic
+    one, and ln V' = 3 eta resp. sum of the axes' eta).  For an ideal gas held at T by the
+    thermostat, P V = (N - 1) kB T, so u = ln(V / V_eq) obeys u'' = -c (e^u - 1) with
+    c = 9 (N - 1) kB T / Q_b (isotropic) or 3 (N - 1) kB T / Q_b (anisotropic: the three axes
+    see the same kinetic pressure on average): small oscillations of the volume at
+    omega tau_P = 3 resp. sqrt(3) (times sqrt((N - 1)/(N + 1))).  An isotropic factor d = 3
+    on each axis of the anisotropic form, or a missing one in the isotropic form, changes
+    omega by sqrt(3)."""
+    n, T, P, tau_p = 4096, 400.0, 0.1 / O.EV_A3_TO_GPA, 0.5
+    kT = O.KB * T
+    v_eq = (n - 1) * kT / P
+    L = (1.1 * v_eq) ** (1.0 / 3.0)
+    box = np.array([L, L * 1.1, L / 1.1])
+    x = np.random.default_rng(1).uniform(0.0, 1.0, (n, 3)) * box
+    s = O.System(x=x, v=I.gaussian_velocities(n, _sv(T), 2), box=box, r0=x.copy(), pot=O.POT_EINSTEIN, k_int=0.0,
+                 T=T, tdamp=0.1, seed=4, baro=baro, p_ext=P, pdamp=tau_p)
+    s.setup()
+    u = []
+    for _ in range(4000):
+        s.step()
+        u.append(math.log(s.volume() / v_eq))
+    u = np.array(u)
+    cross = np.where(np.sign(u[:-1]) != np.sign(u[1:]))[0]
+    assert len(cross) >= 4
+    omega = math.pi / (np.diff(cross[:4]).mean() * s.dt)
+    expect = omega_tau / tau_p * math.sqrt((n - 1) / (n + 1))
+    assert abs(omega / expect - 1.0) < 0.1
+
+
+class _FrozenPhase:
+    """A phase whose per-atom energy and volume stay fixed: what the dCCI update sees when the
+    two phases' dU and dV do not change along the line."""
+
+    def __init__(self, n, u_atom, v_atom):
+        self.n, self.u_int, self.vol = n, n * u_atom, n * v_atom
+        self.f = np.zeros((n, 3))
+
+    def setup(self):
+        pass
+
+    def observe(self):
+        return self.vol, np.zeros(6), 0.0, 0.0, 0.0
+
+    def record(self, *a):
+        pass
+
+    def barostat_kick(self, Pt):
+        pass
+
+    def particle_step(self):
+        pass
+
+
+@pytest.mark.parametrize("mode", [O.DCCI_TEMP, O.DCCI_PRESS])
+def test_dcci_with_constant_latent_heat_follows_the_exact_clausius_clapeyron_line(mode):
+    """With dU and dV per atom constant along the line, the Clausius-Clapeyron equation
+    (Eq. CCE, dP/dT = (dU + P dV) / (T dV) per atom) integrates exactly to
+    P/T = P0/T0 - (dU/dV)(1/T - 1/T0).  The discrete updates (Eqs. Ps_coex_discreted and
+    l_coex_discreted) telescope onto this line, so T_coex = T0/lambda and P_coex = P_S/lambda
+    must lie on it to rounding at every step.  Using dV/dU for dU/dV, or the opposite sign,
+    or the phases the other way round in only one of the two differences, leaves the line."""
+    T0, P0 = 400.0, 13.0 / O.EV_A3_TO_GPA
+    a = _FrozenPhase(8000, -4.25, 20.0)          # cd-like: higher energy, larger volume
+    b = _FrozenPhase(7448, -4.21, 18.5)
+    du, dv = -4.25 - (-4.21), 20.0 - 18.5
+    if mode == O.DCCI_TEMP:
+        pair = O.DcciPair(a, b, T0, P0, mode, T0, 1250.0, 1000)
+    else:
+        pair = O.DcciPair(a, b, T0, P0, mode, P0, 5.0 / O.EV_A3_TO_GPA, 1000)
+    for _ in range(1000):
+        pair.step()
+        T, P = pair.coexistence()
+        exact = T * (P0 / T0 - (du / dv) * (1.0 / T - 1.0 / T0))
+        assert P == pytest.approx(exact, rel=1e-10, abs=1e-14)
+        if mode == O.DCCI_TEMP:
+            assert T == pytest.approx(pair.control(pair.k), rel=1e-12)
+        else:
+            assert P == pytest.approx(pair.control(pair.k), rel=1e-10)
+    assert pair.error == 0
