@@ -20,6 +20,9 @@
  *   orc_neighbor_list   Verlet list by brute force: every j != i whose minimum-image
  *                       distance squared is strictly below (rc + skin)^2, rows ordered by j.
  *   orc_cell_bin        Cell assignment and the stable counting sort by (cell, atom index).
+ *   orc_uf_energy       Uhlenbeck-Ford pair energy, forces and virial by brute force (the
+ *                       fluid reference system the paper uses for the liquid, Sec. 2.1 and
+ *                       Sec. 4, from Paula Leite et al. 2016), truncated and shifted at rc.
  *
  * All floating-point arithmetic is IEEE binary64; build with -ffp-contract=off so that no
  * multiply-add is fused (the integer decisions of the list and the cells then follow the
@@ -399,4 +402,45 @@ int orc_cell_bin(int64_t n, const double* x, const double* box, double rcs, int 
     for (int64_t i = 0; i < n; ++i) perm[fill[cell_of[i]]++] = (int32_t)i;  /* stable */
     free(fill);
     return (int)total;
+}
+
+/*
+ * Uhlenbeck-Ford fluid (the liquid's reference system, Sec. 2.1 and Sec. 4):
+ *   u(r) = -p kT ln(1 - exp(-r^2/sigma^2)) - u(rc)   for r < rc, else 0,
+ * i.e. the UF pair potential with the energy scale p kT (kT fixed by the reference
+ * temperature, not by the thermostat), truncated at rc and shifted there so that the energy
+ * is continuous.  Force on j from i (d = x_j - x_i):  f_j = p kT (2/sigma^2) d / (exp(x) - 1)
+ * with x = r^2/sigma^2 (repulsive).  Every unordered pair once, minimum image; box lengths
+ * must exceed 2 rc.  Virial W_ab = sum over pairs d_a f_j,b.  Per-atom energy: half of each
+ * pair term to each partner.  prm = [p, sigma, kT, rc].  Returns E, or NaN for a small box.
+ */
+double orc_uf_energy(int64_t n, const double* x, const double* box, const double* prm,
+                     double* f, double* vir, double* eatom) {
+    const double p = prm[0], sig = prm[1], kT = prm[2], rc = prm[3];
+    for (int k = 0; k < 3; ++k) if (!(box[k] > 2.0 * rc)) return NAN;
+    const double pk = p * kT, is2 = 1.0 / (sig * sig);
+    const double shift = -pk * log(1.0 - exp(-rc * rc * is2));
+    double E = 0.0, W[9] = {0};
+    if (f) memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    if (eatom) memset(eatom, 0, sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = min_image(x[3 * j + k], x[3 * i + k], box[k], NULL);
+            double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(rr < rc * rc)) continue;
+            double xx = rr * is2;
+            double u = -pk * log(1.0 - exp(-xx)) - shift;
+            double c = 2.0 * pk * is2 / expm1(xx);   /* f_j = c d */
+            E += u;
+            if (eatom) { eatom[i] += 0.5 * u; eatom[j] += 0.5 * u; }
+            if (f) for (int k = 0; k < 3; ++k) { f[3 * j + k] += c * d[k]; f[3 * i + k] -= c * d[k]; }
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) W[3 * a + b] += d[a] * c * d[b];
+        }
+    }
+    if (vir) {
+        vir[0] = W[0]; vir[1] = W[4]; vir[2] = W[8];
+        vir[3] = W[1]; vir[4] = W[2]; vir[5] = W[5];
+    }
+    return E;
 }

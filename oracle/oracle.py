@@ -92,6 +92,8 @@ def lib():
                                         ip, ip, ip]
         L.orc_cell_bin.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_int,
                                    ip, ip, ip, ip]
+        L.orc_uf_energy.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, dp]
+        L.orc_uf_energy.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -182,9 +184,73 @@ def cell_bin(x, box, rcs, ncell_cap=1 << 22):
     return nc3, cell_of, start[: tot + 1].copy(), perm
 
 
+def uf_energy(x, box, uf):
+    """Brute-force Uhlenbeck-Ford energy, forces (n,3), virial (xx,yy,zz,xy,xz,yz) and per-atom
+    energy.  ``uf`` = (p, sigma, T_uf, rc): u(r) = -p kB T_uf ln(1 - exp(-r^2/sigma^2)) - u(rc) for
+    r < rc (Sec. 2.1 names the UF model as the fluid reference; Sec. 4 uses p = 25, sigma = 2.0)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    p = np.array([uf[0], uf[1], KB * uf[2], uf[3]], dtype=np.float64)
+    f = np.zeros((n, 3))
+    vir = np.zeros(6)
+    ea = np.zeros(n)
+    e = lib().orc_uf_energy(n, _p(x), _p(box), _p(p), _p(f), _p(vir), _p(ea))
+    if math.isnan(e):
+        raise ValueError("orc_uf_energy: box smaller than 2 rc")
+    return e, f, vir, ea
+
+
 # ------------------------------------------------------------------------------------------
 # Closed forms and estimators
 # ------------------------------------------------------------------------------------------
+def _uf_mayer_coefficients(p: int):
+    """The UF Mayer function exp(-u/kT) - 1 = (1 - exp(-r^2/sigma^2))^p - 1 expanded by the
+    binomial theorem: sum_{k=1..p} C(p, k) (-1)^k exp(-k r^2/sigma^2) (integer p)."""
+    if int(p) != p or p < 1:
+        raise ValueError("the closed forms need an integer p >= 1")
+    p = int(p)
+    return [(k, math.comb(p, k) * (-1) ** k) for k in range(1, p + 1)]
+
+
+def uf_b2(p: int, sigma: float) -> float:
+    """Second virial coefficient of the untruncated UF fluid, B2 = -1/2 int f d^3r with the
+    Gaussian expansion of the Mayer function: int exp(-k r^2/sigma^2) d^3r = (pi/k)^(3/2) sigma^3,
+    so B2 = -(pi^(3/2) sigma^3 / 2) sum_k C(p,k) (-1)^k k^(-3/2)."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    s = sum(Decimal(c) / (Decimal(k) * Decimal(k).sqrt()) for k, c in _uf_mayer_coefficients(p))
+    return -0.5 * math.pi ** 1.5 * sigma ** 3 * float(s)
+
+
+def uf_b3(p: int, sigma: float) -> float:
+    """Third virial coefficient of the untruncated UF fluid, B3 = -1/3 int int f12 f13 f23,
+    from the same expansion and the Gaussian integral
+    int int exp(-a x^2 - b y^2 - c |x - y|^2) d^3x d^3y = (pi^2 / (ab + bc + ca))^(3/2):
+    B3 = -(pi^3 sigma^6 / 3) sum_{k,l,m} c_k c_l c_m (kl + lm + mk)^(-3/2).  The alternating
+    binomial sums cancel over many digits, so they are summed in 60-digit decimal arithmetic."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    cs = _uf_mayer_coefficients(p)
+    s = Decimal(0)
+    for k, ck in cs:
+        for l, cl in cs:
+            for m, cm in cs:
+                q = Decimal(k * l + l * m + m * k)
+                s += Decimal(ck * cl * cm) / (q * q.sqrt())
+    return -(math.pi ** 3) * sigma ** 6 / 3.0 * float(s)
+
+
+def ideal_gas_free_energy(n: int, volume: float, T: float, mass: float = M_SI) -> float:
+    """Classical ideal gas of n identical atoms in volume V: F = -kB T ln(V^n / (n! Lambda^(3n)))
+    with the thermal wavelength Lambda = hbar sqrt(2 pi / (m kB T)) (the end state of the
+    switching that gives the UF fluid's free energy)."""
+    kT = KB * T
+    lam = HBAR * math.sqrt(2.0 * math.pi / (mass * MVV2E * kT))
+    return -kT * (n * math.log(volume / lam ** 3) - math.lgamma(n + 1.0))
+
+
+
 def einstein_free_energy(n: int, k: float, T: float, mass: float = M_SI) -> float:
     """Classical Einstein crystal, 3N independent oscillators of frequency sqrt(k/m):
     F = 3 N kB T ln(hbar omega / kB T).  The paper only says this F is known analytically
@@ -256,7 +322,8 @@ def dcci_press_update(lam_k, p_k, p_k1, du, dv):
 # Time integration of one system, or of a coupled dCCI pair
 # ------------------------------------------------------------------------------------------
 SCHED_NONE, SCHED_FL, SCHED_RS, SCHED_AS = 0, 1, 2, 3
-POT_SW, POT_EINSTEIN = 0, 1
+POT_SW, POT_EINSTEIN, POT_UF = 0, 1, 2
+REF_EINSTEIN, REF_UF = 0, 1
 BARO_NONE, BARO_ISO, BARO_ANISO = 0, 1, 2
 DCCI_TEMP, DCCI_PRESS = 0, 1
 DEGEN_DV = 1e-6      # A^3/atom: |dV| below this makes the temperature-control update singular
@@ -272,8 +339,11 @@ class System:
     0 -> 1 along ``fl_lambda``; RS is H = K + lambda U_int + lambda P V along ``rs_lambda``
     (forward 1 -> lambda_f); AS drives the barostat pressure linearly P0 -> P1 and its
     driving force is V.  ``direction`` = -1 runs FL/RS backward (tau -> 1 - tau).
-    ``pot`` selects U_int: Stillinger-Weber, or (test mode) an Einstein crystal with spring
-    ``k_int`` about r0 whose free energy is known in closed form.
+    ``pot`` selects U_int: Stillinger-Weber, the Uhlenbeck-Ford fluid (parameters ``uf``), or
+    (test mode) an Einstein crystal with spring ``k_int`` about r0 whose free energy is known in
+    closed form (k_int = 0: no interaction, the ideal gas).  ``ref`` selects U_E of the FL
+    interpolation: the Einstein crystal (springs k_E about r0) for solids, or the UF fluid for
+    the liquid (Sec. 2.1: "for fluid-phase systems ... the Uhlenbeck-Ford model").
     """
     x: np.ndarray
     v: np.ndarray
@@ -300,6 +370,8 @@ class System:
     p1: float = 0.0           # AS
     lam: float = 1.0
     trace_every: int = 0
+    ref: int = REF_EINSTEIN
+    uf: tuple = (25.0, 2.0, 2200.0, 8.0)   # p, sigma (A), T_uf (K), rc (A)
     # dynamic state
     f: np.ndarray | None = None
     eta: np.ndarray = field(default_factory=lambda: np.zeros(3))
@@ -355,12 +427,21 @@ class System:
             self.u_int = e
             self.vir = vir
             f += s_int * fsw
+        elif self.pot == POT_UF:
+            e, fuf, vir, _ = uf_energy(self.x, self.box, self.uf)
+            self.u_int = e
+            self.vir = vir
+            f += s_int * fuf
         else:
             d = self.x - self.r0
             self.u_int = 0.5 * self.k_int * float(np.sum(d * d))
             self.vir = np.zeros(6)
             f += s_int * (-self.k_int * d)
-        if self.k_E > 0.0 and self.r0 is not None:
+        if self.sched == SCHED_FL and self.ref == REF_UF:
+            e, fuf, _, _ = uf_energy(self.x, self.box, self.uf)
+            self.u_ref = e
+            f += s_e * fuf
+        elif self.k_E > 0.0 and self.r0 is not None:
             d = self.x - self.r0
             self.u_ref = 0.5 * self.k_E * float(np.sum(d * d))
             f += s_e * (-self.k_E * d)

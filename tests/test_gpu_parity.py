@@ -210,8 +210,9 @@ def test_frenkel_ladd_trajectory_fp64_matches_oracle(N):
 def test_frenkel_ladd_trajectory_fp32_close_to_oracle(N, lanes):
     orc, res, x, v = _fl_pair(0, nsteps=100, lanes=lanes)
     ro = orc.results()
-    assert np.abs(x - orc.x).max() < 1e-4
-    assert res["W"] == pytest.approx(ro["W"], rel=1e-3, abs=1e-3)
+    # 100 FP32 steps of the 64-atom crystal stay within 3e-6 A and 1.3e-7 of W (measured on GB300)
+    assert np.abs(x - orc.x).max() < 2e-5
+    assert res["W"] == pytest.approx(ro["W"], rel=1e-6, abs=1e-9)
     assert res["U"] == pytest.approx(ro["U"], rel=1e-5)
 
 

@@ -631,3 +631,127 @@ def test_dcci_with_constant_latent_heat_follows_the_exact_clausius_clapeyron_lin
         else:
             assert P == pytest.approx(pair.control(pair.k), rel=1e-10)
     assert pair.error == 0
+
+
+# ---------------------------------------------------------------- Uhlenbeck-Ford fluid reference
+UF = (25.0, 2.0, 2200.0, 8.0)      # p, sigma (A), T_uf (K), rc (A): the liquid reference of Sec. 4
+
+
+def _uf_dimer(r, rc=14.0):
+    x = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+    return O.uf_energy(x, np.array([30.0, 30.0, 30.0]), (UF[0], UF[1], UF[2], rc))
+
+
+def test_uf_second_virial_coefficient_closed_form():
+    """B2 = -1/2 int (exp(-u/kT) - 1) d^3r: by quadrature of the oracle's own dimer energy
+    (truncated at 7 sigma, where the Mayer function is e^-49) against the Gaussian-sum
+    closed form, and the closed form against quadrature of (1 - exp(-r^2/sigma^2))^p - 1."""
+    from scipy import integrate
+    p, sig, T = UF[0], UF[1], UF[2]
+    kT = O.KB * T
+    b2 = O.uf_b2(int(p), sig)
+    mayer = lambda r: (math.exp(-_uf_dimer(r)[0] / kT) - 1.0) * r * r
+    q = integrate.quad(mayer, 1e-9, 14.0, limit=400, epsabs=1e-12, epsrel=1e-12)[0]
+    assert -2.0 * math.pi * q == pytest.approx(b2, rel=1e-7)
+    q2 = integrate.quad(lambda r: ((1.0 - math.exp(-(r / sig) ** 2)) ** p - 1.0) * r * r, 0.0, 30.0,
+                        limit=400, epsabs=1e-13, epsrel=1e-13)[0]
+    assert -2.0 * math.pi * q2 == pytest.approx(b2, rel=1e-10)
+    # the potential is repulsive, continuous at rc and zero beyond
+    e, f, _, _ = _uf_dimer(3.0, rc=8.0)
+    assert e > 0.0 and f[1, 0] > 0.0 and f[0, 0] == -f[1, 0]
+    assert _uf_dimer(8.0 - 1e-9, rc=8.0)[0] == pytest.approx(0.0, abs=1e-12)
+    assert _uf_dimer(8.0 + 1e-9, rc=8.0)[0] == 0.0
+
+
+def test_uf_third_virial_coefficient_closed_form():
+    """B3 = -(8 pi^2 / 3) int int f(r) f(s) r^2 s^2 int_-1^1 f(sqrt(r^2 + s^2 - 2 r s c)) dc dr ds
+    by Gauss-Legendre quadrature against the Gaussian-sum closed form."""
+    p, sig = int(UF[0]), UF[1]
+    f = lambda r: (1.0 - np.exp(-(r / sig) ** 2)) ** p - 1.0
+    xr, wr = np.polynomial.legendre.leggauss(160)
+    xc, wc = np.polynomial.legendre.leggauss(96)
+    rmax = 6.0 * sig
+    r = 0.5 * rmax * (xr + 1.0)
+    w = 0.5 * rmax * wr
+    R, S, C = np.meshgrid(r, r, xc, indexing="ij")
+    inner = (f(np.sqrt(R * R + S * S - 2.0 * R * S * C)) * wc[None, None, :]).sum(axis=2)
+    fr = f(r) * r * r * w
+    b3 = -(8.0 * math.pi ** 2 / 3.0) * float(fr @ inner @ fr)
+    assert b3 == pytest.approx(O.uf_b3(p, sig), rel=1e-6)
+
+
+def test_uf_forces_and_virial_are_derivatives():
+    x, box = I.liquid(300, 0.05, seed=12, rmin=1.0)
+    e, f, vir, ea = O.uf_energy(x, box, UF)
+    h = 1e-5
+    fd = np.zeros_like(x)
+    for i in range(0, len(x), 7):
+        for k in range(3):
+            xp = x.copy(); xp[i, k] += h
+            xm = x.copy(); xm[i, k] -= h
+            fd[i, k] = -(O.uf_energy(xp, box, UF)[0] - O.uf_energy(xm, box, UF)[0]) / (2 * h)
+    sel = np.arange(0, len(x), 7)
+    assert np.abs(fd[sel] - f[sel]).max() < 1e-6 * np.abs(f).max()
+    assert np.abs(f.sum(axis=0)).max() < 1e-10
+    assert ea.sum() == pytest.approx(e, rel=1e-12)
+    # virial = -dE/d(strain): W_aa = -L_a dE/dL_a under affine scaling of axis a
+    for a in range(3):
+        s = np.ones(3); s[a] = 1.0 + h
+        ep = O.uf_energy(x * s, box * s, UF)[0]
+        s[a] = 1.0 - h
+        em = O.uf_energy(x * s, box * s, UF)[0]
+        assert vir[a] == pytest.approx(-(ep - em) / (2 * h), rel=1e-6, abs=1e-8)
+
+
+def test_ideal_gas_free_energy_sackur_tetrode():
+    """The classical ideal-gas free energy (the end state of the switching to the UF fluid)
+    gives the Sackur-Tetrode entropy S = (U - F)/T: argon at 298.15 K and 1 bar against its
+    tabulated standard entropy."""
+    g = _golden("ideal_gas.txt")
+    T, n = 298.15, 10 ** 6
+    kT = O.KB * T
+    e_charge, n_a = 1.602176634e-19, 6.02214076e23
+    V = n * kT / (1e5 * 1e-30 / e_charge)          # 1 bar in eV/A^3
+    F = O.ideal_gas_free_energy(n, V, T, g["argon_mass_g_per_mol"])
+    S = (1.5 * n * kT - F) / T / n * e_charge * n_a
+    assert S == pytest.approx(g["argon_S298_J_per_K_mol"], abs=0.005)
+
+
+def _uf_switch_work(n, box, direction, seed, nsw):
+    T = UF[2]
+    x = np.random.default_rng(seed).uniform(0.0, 1.0, (n, 3)) * box
+    pot = O.POT_EINSTEIN if direction > 0 else O.POT_UF
+    eq = O.System(x=x, v=I.gaussian_velocities(n, _sv(T), seed), box=box.copy(), r0=x.copy(), pot=pot,
+                  k_int=0.0, uf=UF, T=T, tdamp=0.1, seed=seed, sys_id=1)
+    eq.run(500)
+    sw = O.System(x=eq.x, v=eq.v, box=box.copy(), r0=x.copy(), pot=O.POT_EINSTEIN, k_int=0.0, ref=O.REF_UF,
+                  uf=UF, T=T, tdamp=0.1, seed=seed, sys_id=2, sched=O.SCHED_FL, direction=direction, nsched=nsw)
+    sw.run(nsw)
+    return sw.W
+
+
+def test_ideal_gas_to_uf_switching_follows_the_virial_series():
+    """Hamiltonian interpolation from the ideal gas (lambda = 0) to the UF fluid (lambda = 1)
+    at low density: the excess free energy of n atoms in a periodic box is
+    F_ex / (n kT) = (n-1)/n rho B2 + (n-1)(n-2)/n^2 rho^2 B3 / 2 + O(rho^3) (pair and triplet
+    counting of the cluster expansion).  At rho B2 = 0.2 the B3 term is 5 % of the total and
+    the B4 term about 0.5 %; 8 + 8 realisations of 6000 steps, 128 atoms."""
+    n, target = 128, 0.2
+    p, sig, T = int(UF[0]), UF[1], UF[2]
+    b2, b3 = O.uf_b2(p, sig), O.uf_b3(p, sig)
+    rho = target / b2
+    L = (n / rho) ** (1.0 / 3.0)
+    box = np.array([L, L, L])
+    reps, nsw = 8, 6000
+    wf = np.array([_uf_switch_work(n, box, +1, s, nsw) for s in range(reps)])
+    wb = np.array([_uf_switch_work(n, box, -1, 100 + s, nsw) for s in range(reps)])
+    kT = O.KB * T
+    fex = O.free_energy_difference(wf, wb) / (n * kT)
+    sem = 0.5 * math.sqrt(wf.var(ddof=1) / reps + wb.var(ddof=1) / reps) / (n * kT)
+    pred = (n - 1) / n * rho * b2 + (n - 1) * (n - 2) / n ** 2 * rho ** 2 * b3 / 2.0
+    assert sem < 0.01
+    assert abs(fex - pred) < 4.0 * sem + 0.002
+    assert O.dissipated_heat(wf, wb) > 0.0
+    # the free energy of the interacting fluid, Eq. dA with the ideal gas as reference
+    f_uf = O.ideal_gas_free_energy(n, L ** 3, T) + O.free_energy_difference(wf, wb)
+    assert f_uf > O.ideal_gas_free_energy(n, L ** 3, T)
