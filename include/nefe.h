@@ -79,6 +79,23 @@ typedef struct nefe_sw_params {
 /* Fills *out with the standard silicon set above.  Never fails for a non-NULL out. */
 NEFE_API int nefe_sw_params_silicon(nefe_sw_params* out);
 
+/* Reference system of the Hamiltonian interpolation (NEFE_SCHED_FL, Sec. 2.1): the Einstein
+ * crystal for solids, the Uhlenbeck-Ford fluid for liquids. */
+#define NEFE_REF_EINSTEIN 0
+#define NEFE_REF_UF       1
+
+/* Uhlenbeck-Ford fluid (Sec. 2.1 names it the fluid-phase reference, Paula Leite et al. 2016;
+ * Sec. 4 uses p = 25, sigma = 2.0 for liquid Si at 2200 K):
+ *   u(r) = -p kB T ln(1 - exp(-r^2/sigma^2)) - u(rc)  for r < rc, else 0,
+ * truncated at rc and shifted so that the energy is continuous there.  T is the reference's
+ * own temperature (it sets the energy scale p kB T; it need not equal the thermostat's).
+ * The pair list radius is rc + skin and must not exceed 2 (a sigma + skin) (the cells of the
+ * SW list are reused with a +-2 cell stencil); rows hold at most NEFE_UF_CAP neighbours.    */
+typedef struct nefe_uf_params {
+    double p, sigma, T, rc;
+} nefe_uf_params;
+#define NEFE_UF_CAP 256
+
 /* ---------------------------------------------------------------- stateless kernels */
 /*
  * nefe_cell_bin - cell grid, cell of each atom and the stable counting sort by cell.
@@ -175,6 +192,25 @@ NEFE_API int nefe_sw_forces(const double* x, int n, const double box[3], double 
                    int* shell_overflow, void* stream);
 
 /*
+ * nefe_uf_forces - Uhlenbeck-Ford energy, forces and virial (the fluid reference of Sec. 2.1;
+ * functional form above), each pair within rc once, minimum image.  The list (radius rc +
+ * skin, the cells of a SW list of radius rcs, a +-2 cell stencil) is built inside the call.
+ *   x, n, box   device FP64 SoA [3n] positions, atoms, host box [3]; every box length must be
+ *               >= 2 (rc + skin) and give >= 5 cells of width >= rcs.
+ *   rcs, skin   cell criterion and list skin (rc + skin <= 2 rcs).
+ *   uf          host, UF parameters.
+ *   precision   NEFE_FP32 or NEFE_FP64 pair arithmetic (sums in fixed point, order independent).
+ *   f           device out FP64 SoA [3n]; e_atom device out [n] or NULL (half of each pair);
+ *   energy_virial device out [7] or NULL: E and the virial xx yy zz xy xz yz.
+ * Scratch is allocated stream-ordered and released on the stream.  Returns NEFE_EINVAL on bad
+ * arguments, NEFE_EOVERFLOW when a row exceeds NEFE_UF_CAP, NEFE_ENOMEM / NEFE_ECUDA.
+ * Blocking: yes (reads the overflow flag).
+ */
+NEFE_API int nefe_uf_forces(const double* x, int n, const double box[3], double rcs, double skin,
+                            const nefe_uf_params* uf, int precision, double* f, double* e_atom,
+                            double* energy_virial, void* stream);
+
+/*
  * nefe_sw_energy_grad - the SW energy, forces and the derivatives of the energy with respect to
  * the potential parameters theta = (A, B, p, q, a, lambda3, gamma) (eps, sigma, cos0 fixed), for
  * differentiating the model (the backward of an energy function).  Pair terms give
@@ -207,7 +243,10 @@ NEFE_API int nefe_langevin_noise(uint64_t seed, uint64_t sys_id, uint64_t step, 
 typedef struct nefe_ctx nefe_ctx;
 
 #define NEFE_POT_SW       0   /* U_int = Stillinger-Weber                                */
-#define NEFE_POT_EINSTEIN 1   /* U_int = k_int/2 sum |x - r0|^2 (closed-form test system) */
+#define NEFE_POT_EINSTEIN 1   /* U_int = k_int/2 sum |x - r0|^2 (closed-form test system; */
+                              /*   k_int = 0 is the ideal gas)                             */
+#define NEFE_POT_UF       2   /* U_int = Uhlenbeck-Ford fluid (nefe_set_uf_params)         */
+
 
 #define NEFE_BARO_NONE  0
 #define NEFE_BARO_ISO   1
@@ -245,6 +284,8 @@ typedef struct nefe_schedule {
     double P_GPa;              /* RS: physical pressure P (target is lambda P)              */
     double P0_GPa, P1_GPa;     /* AS: pressure path                                        */
     double lambda0;            /* NONE: fixed lambda (force scale on U_int)                 */
+    int ref;                   /* FL: NEFE_REF_EINSTEIN (springs k_E about r0) or NEFE_REF_UF */
+                               /*   (the system's UF parameters); 0 = Einstein              */
 } nefe_schedule;
 
 /* Results of one system after the last completed step (FP64).  H and dH/dl follow the
@@ -289,6 +330,11 @@ NEFE_API const char* nefe_last_error(void);
 NEFE_API int nefe_add_system(nefe_ctx* ctx, const nefe_system_desc* desc, int* sys_id);
 /* Potential parameters for one system, or all systems when sys == -1. */
 NEFE_API int nefe_set_sw_params(nefe_ctx* ctx, int sys, const nefe_sw_params* prm);
+/* Uhlenbeck-Ford parameters of one system (used when its pot is NEFE_POT_UF or its FL
+ * reference is NEFE_REF_UF).  Default: p = 25, sigma = 2.0 A, T = 2200 K, rc = 8.0 A.
+ * NEFE_EINVAL on p <= 0, sigma <= 0, T <= 0 or rc <= 0; NEFE_ESTATE after setup.  The
+ * cutoff condition rc + skin <= 2 (a sigma + skin) is checked by nefe_setup. */
+NEFE_API int nefe_set_uf_params(nefe_ctx* ctx, int sys, const nefe_uf_params* uf);
 /* Langevin thermostat: T (K), damping time (ps; <= 0 switches it off), noise seed.
  * The random force of each step has its per-system mean removed ("zero yes", Sec. 4). */
 NEFE_API int nefe_set_thermostat(nefe_ctx* ctx, int sys, double T, double damp_ps, uint64_t seed);

@@ -48,7 +48,7 @@ int check_box(const double box[3], double rcs) {
 }
 
 int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap, int prec,
-                    bool cells) {
+                    bool cells, const nefe_uf_params* uf, double skin) {
     const int ntiles = (n + kTile - 1) / kTile;
     DevSys hs;
     std::memset(&hs, 0, sizeof(hs));
@@ -56,6 +56,10 @@ int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap,
     hs.rcs = rcs; hs.pair = -1; hs.prm = 0; hs.mass_e = 1.0;
     hs.rcs2_lo_f = (float)(rcs * rcs) * (1.0f - 1e-4f);
     hs.rcs2_hi_f = (float)(rcs * rcs) * (1.0f + 1e-4f);
+    if (uf) {
+        fill_uf(hs, *uf, skin, UF_INT);
+        hs.pot = POT_UF;
+    }
     DevState st;
     std::memset(&st, 0, sizeof(st));
     for (int k = 0; k < 3; ++k) st.box[k] = box[k];
@@ -273,6 +277,53 @@ int nefe_sw_energy_grad(const double* x, int n, const double box[3], double rcs,
     if (st.err & NEFE_ERR_SHELL_OVERFLOW)
         return fail(NEFE_EOVERFLOW, "nefe_sw_energy_grad: shell above 32 neighbours");
     if (st.err & NEFE_ERR_NAN) return fail(NEFE_ENAN, "nefe_sw_energy_grad: non-finite sum");
+    return NEFE_OK;
+}
+
+int nefe_uf_forces(const double* x, int n, const double box[3], double rcs, double skin,
+                   const nefe_uf_params* uf, int precision, double* f, double* e_atom,
+                   double* energy_virial, void* stream) {
+    if (n < 0 || !box || !valid_uf(uf) || !(skin >= 0.0) || (precision != NEFE_FP32 && precision != NEFE_FP64) ||
+        (n > 0 && (!x || !f)))
+        return fail(NEFE_EINVAL, "nefe_uf_forces: bad argument");
+    if (n >= (1 << kUfShift)) return fail(NEFE_EINVAL, "nefe_uf_forces: n above 2^25");
+    int rc = check_box(box, rcs);
+    if (rc) return rc;
+    const double R = uf->rc + skin;
+    if (R > 2.0 * rcs) return fail(NEFE_EINVAL, "nefe_uf_forces: rc + skin = %g above 2 rcs = %g", R, 2.0 * rcs);
+    int n3[3];
+    if (!host_grid(box, rcs, n3)) return fail(NEFE_EINVAL, "nefe_uf_forces: fewer than 2 cells on an axis");
+    for (int k = 0; k < 3; ++k) {
+        if (n3[k] < 5) return fail(NEFE_EINVAL, "nefe_uf_forces: fewer than 5 cells on an axis");
+        if (box[k] < 2.0 * R) return fail(NEFE_EINVAL, "nefe_uf_forces: box below 2 (rc + skin)");
+    }
+    const long long total = (long long)n3[0] * n3[1] * n3[2];
+    if (total > (1LL << 30)) return fail(NEFE_EINVAL, "nefe_uf_forces: cell grid too large");
+    Scratch1 S;
+    S.s = (cudaStream_t)stream;
+    rc = prepare1(S, n, box, rcs, (int)total, precision, true, uf, skin);
+    if (rc) return rc;
+    if (n > 0) {
+        int* uf_nbr = nullptr;
+        int* uf_cnt = nullptr;
+        NEFE_CU(S.alloc(&uf_nbr, sizeof(int) * (size_t)n * kUfCap));
+        NEFE_CU(S.alloc(&uf_cnt, sizeof(int) * (size_t)n));
+        Bufs b = bufs_of(S, x, n);
+        b.uf_nbr = uf_nbr; b.uf_cnt = uf_cnt; b.uf_tiles = nullptr;
+        b.f_out = f; b.e_atom = e_atom;
+        const int ntiles = (n + kTile - 1) / kTile;
+        launch_cells(b, precision, ntiles, 1, 1, S.s, nullptr);
+        launch_uf_list(b, precision, ntiles, S.s, nullptr);
+        launch_uf(b, precision, ntiles, FM_FORCES, S.s, nullptr);
+        NEFE_CU(cudaGetLastError());
+    }
+    if (energy_virial) launch_decode_ev(S.acc, energy_virial, S.s);
+    NEFE_CU(cudaGetLastError());
+    DevState st;
+    NEFE_CU(cudaMemcpyAsync(&st, S.st, sizeof(st), cudaMemcpyDeviceToHost, S.s));
+    NEFE_CU(cudaStreamSynchronize(S.s));
+    if (st.err & NEFE_ERR_NBR_OVERFLOW) return fail(NEFE_EOVERFLOW, "nefe_uf_forces: a row exceeded %d", kUfCap);
+    if (st.err & (NEFE_ERR_BOX | NEFE_ERR_CELL)) return fail(NEFE_EINVAL, "nefe_uf_forces: cell grid error");
     return NEFE_OK;
 }
 

@@ -16,6 +16,11 @@ constexpr int kSpill1 = 12;       // thread-per-atom pass A: shell entries kept 
 constexpr int kMaxCap = 64;       // max neighbour row capacity (one 64-bit slot mask per atom)
 constexpr int kCodeShift = 27;    // nbr entry = j | (cell-offset code << 27)
 constexpr uint32_t kIndexMask = (1u << kCodeShift) - 1u;
+// Uhlenbeck-Ford pair list: entry = j | (code << 25), code = (ox+2) + 5 (oy+2) + 25 (oz+2) for the
+// cell offset o in {-2..2}^3 through which j was reached.
+constexpr int kUfCap = 256;
+constexpr int kUfShift = 25;
+constexpr uint32_t kUfMask = (1u << kUfShift) - 1u;
 
 // Fixed-point accumulators: per-system sums are accumulated as int64 in units of 2^-32,
 // so the order in which blocks add them does not change the result (bitwise determinism).
@@ -31,7 +36,8 @@ enum Acc {
 };
 
 enum Sched { SCHED_NONE = 0, SCHED_FL = 1, SCHED_RS = 2, SCHED_AS = 3 };
-enum Pot { POT_SW = 0, POT_EINSTEIN = 1 };
+enum Pot { POT_SW = 0, POT_EINSTEIN = 1, POT_UF = 2 };
+enum UfMode { UF_NONE = 0, UF_INT = 1, UF_REF = 2 };   // UF as U_int, or as the FL reference
 enum Baro { BARO_NONE = 0, BARO_ISO = 1, BARO_ANISO = 2 };
 
 // Potential constants in the precision of the force kernel.
@@ -77,6 +83,10 @@ struct DevSys {
     int trace_every;
     long long trace_cap, trace_off;
     int prm;                    // index into the parameter tables
+    // Uhlenbeck-Ford term: u = -pk ln(1 - exp(-r^2 is2)) - shift for r^2 < rc2
+    int uf_mode;                // UfMode
+    double uf_pk, uf_is2, uf_rc2, uf_shift, uf_R2;   // p kB T (eV), 1/sigma^2, rc^2, u(rc), list radius^2
+    float uf_pk_f, uf_is2_f, uf_rc2_f, uf_shift_f, uf_R2_f;
 };
 
 // Per-system dynamic state.

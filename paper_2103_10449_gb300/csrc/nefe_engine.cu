@@ -28,6 +28,7 @@ struct HostSys {
     int pot = NEFE_POT_SW;
     double k_int = 0.0;
     nefe_sw_params prm{};
+    nefe_uf_params uf{25.0, 2.0, 2200.0, 8.0};
     double T = 0.0, tdamp = 0.0;
     uint64_t seed = 0;
     int baro = NEFE_BARO_NONE;
@@ -68,6 +69,9 @@ struct nefe_ctx {
     void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_xcs = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
     void *d_shd = nullptr, *d_P = nullptr, *d_spill = nullptr;
     int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr;
+    int *d_uf_nbr = nullptr, *d_uf_cnt = nullptr, *d_uf_tiles = nullptr;
+    void* d_uf_F = nullptr;
+    int n_uf_tiles = 0;      // tiles of the systems with a Uhlenbeck-Ford term
     int4* d_q = nullptr;
     int *d_cell_of = nullptr, *d_perm = nullptr, *d_cell_start = nullptr, *d_cell_count = nullptr,
         *d_cell_cursor = nullptr, *d_nbr = nullptr, *d_cnt = nullptr;
@@ -97,8 +101,10 @@ struct nefe_ctx {
 namespace {
 
 // Per MD step: group update, kick/drift, rebuild worklist, cell count, scan, fill, list build,
-// and the two force passes per chunk.
-int launches_per_step(const nefe_ctx* c) { return 7 + 2 * (int)c->chunk_tile0.size(); }
+// and the two force passes per chunk (with UF systems: their list build and force kernel).
+int launches_per_step(const nefe_ctx* c) {
+    return 7 + 2 * (int)c->chunk_tile0.size() + (c->n_uf_tiles > 0 ? 2 : 0);
+}
 
 // Groups whole systems into chunks of at most `atoms` atoms (a larger system is a chunk of
 // its own).
@@ -151,6 +157,7 @@ double rc_of(const HostSys& h) { return h.prm.a * h.prm.sigma; }
 // Both force passes, chunk by chunk; with slot >= 0 (profiling capture) events bracket
 // every chunk's pass A and pass B.
 void enqueue_forces(nefe_ctx* c, int mode, int slot = -1) {
+    if (c->n_uf_tiles > 0) launch_uf(c->b, c->prec, c->n_uf_tiles, mode, c->stream, &c->launches);
     const int nch = (int)c->chunk_tile0.size();
     for (int k = 0; k < nch; ++k) {
         Bufs b = c->b;
@@ -169,6 +176,7 @@ void enqueue_step(nefe_ctx* c, int slot = -1) {
     launch_group(c->b, c->d_groups, c->ngroups, 1, c->stream, &c->launches);
     launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches);
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
+    if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
     enqueue_forces(c, FM_STEP, slot);
 }
 
@@ -204,6 +212,7 @@ void fill_results(const DevSys& S, const DevState& st, nefe_results* out) {
 int resetup(nefe_ctx* c) {
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * (size_t)c->nsys * ACC_N * kSlots, c->stream));
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 1, c->stream, &c->launches);
+    if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
     launch_kick_drift(c->b, c->prec, c->ntiles, 0, c->stream, &c->launches);
     enqueue_forces(c, FM_SETUP);
     NEFE_CU(cudaGetLastError());
@@ -268,7 +277,22 @@ int setup(nefe_ctx* c) {
         d.direction = h.sched.direction < 0 ? -1 : 1;
         d.nsched = h.sched.nsteps > 0 ? h.sched.nsteps : 1;
         d.k_int = h.k_int;
-        d.k_E = h.sched.kind == NEFE_SCHED_FL ? h.sched.k_E : 0.0;
+        const bool uf_ref = h.sched.kind == NEFE_SCHED_FL && h.sched.ref == NEFE_REF_UF;
+        d.k_E = (h.sched.kind == NEFE_SCHED_FL && !uf_ref) ? h.sched.k_E : 0.0;
+        d.uf_mode = h.pot == NEFE_POT_UF ? UF_INT : (uf_ref ? UF_REF : UF_NONE);
+        if (h.pot == NEFE_POT_UF && uf_ref)
+            return fail(NEFE_EINVAL, "system %d: the UF fluid cannot be its own FL reference", s);
+        if (d.uf_mode != UF_NONE) {
+            fill_uf(d, h.uf, c->skin, d.uf_mode);
+            const double R = h.uf.rc + c->skin;
+            if (R > 2.0 * rcs)
+                return fail(NEFE_EINVAL, "system %d: UF rc + skin = %g above 2 (a sigma + skin) = %g", s, R, 2.0 * rcs);
+            for (int k = 0; k < 3; ++k) {
+                if (h.box[k] < 2.0 * R)
+                    return fail(NEFE_EINVAL, "system %d: box %g below 2 (UF rc + skin) = %g", s, h.box[k], 2.0 * R);
+                if (n3[k] < 5) return fail(NEFE_EINVAL, "system %d: a UF system needs >= 5 cells per axis", s);
+            }
+        }
         d.lam_f = h.sched.lambda_f;
         d.p_phys = h.sched.P_GPa / kEvA3ToGPa;
         d.p0 = h.sched.P0_GPa / kEvA3ToGPa;
@@ -310,6 +334,12 @@ int setup(nefe_ctx* c) {
         tr += h.trace_every > 0 ? h.trace_cap : 0;
     }
     if (ntot >= (1LL << kCodeShift)) return fail(NEFE_EINVAL, "more than 2^27 atoms in one context");
+    std::vector<int> uf_tiles;
+    for (int s = 0; s < nsys; ++s)
+        if (hs[s].uf_mode != UF_NONE)
+            for (int t = 0; t < hs[s].ntile; ++t) uf_tiles.push_back(hs[s].tile0 + t);
+    if (!uf_tiles.empty() && ntot >= (1LL << kUfShift))
+        return fail(NEFE_EINVAL, "more than 2^25 atoms in a context with UF systems");
     c->sys_tile0.resize(nsys);
     c->sys_n.resize(nsys);
     for (int s = 0; s < nsys; ++s) { c->sys_tile0[s] = hs[s].tile0; c->sys_n[s] = hs[s].n; }
@@ -381,6 +411,16 @@ int setup(nefe_ctx* c) {
     if ((rc = dalloc(c, &c->d_pairs, sizeof(DevPair) * std::max<size_t>(1, hp.size())))) return rc;
     if ((rc = dalloc(c, &c->d_groups, sizeof(DevGroup) * groups.size()))) return rc;
     if ((rc = dalloc(c, &c->d_trace, sizeof(double) * 9 * (size_t)std::max<long long>(1, tr)))) return rc;
+    c->n_uf_tiles = (int)uf_tiles.size();
+    if (!uf_tiles.empty()) {
+        if ((rc = dalloc(c, &c->d_uf_nbr, sizeof(int) * N * (size_t)kUfCap))) return rc;
+        if ((rc = dalloc(c, &c->d_uf_cnt, sizeof(int) * N))) return rc;
+        if ((rc = dalloc(c, &c->d_uf_F, v4 * N))) return rc;
+        if ((rc = dalloc(c, &c->d_uf_tiles, sizeof(int) * uf_tiles.size()))) return rc;
+        NEFE_CU(cudaMemcpy(c->d_uf_tiles, uf_tiles.data(), sizeof(int) * uf_tiles.size(), cudaMemcpyHostToDevice));
+        NEFE_CU(cudaMemset(c->d_uf_cnt, 0, sizeof(int) * N));
+        NEFE_CU(cudaMemset(c->d_uf_F, 0, v4 * N));
+    }
     if (c->prec == NEFE_FP64) {
         std::vector<SWc<double>> t(nsys);
         for (int s = 0; s < nsys; ++s) t[s] = make_swc<double>(c->sys[s].prm);
@@ -432,6 +472,7 @@ int setup(nefe_ctx* c) {
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;
     b.trace = c->d_trace;
     b.list_lanes = c->llanes;
+    b.uf_nbr = c->d_uf_nbr; b.uf_cnt = c->d_uf_cnt; b.uf_F = c->d_uf_F; b.uf_tiles = c->d_uf_tiles;
 
     launch_inject(b, c->prec, c->ntiles, nullptr, c->d_vtmp, c->stream);
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * nsys * ACC_N * kSlots, c->stream));
@@ -501,7 +542,8 @@ int nefe_add_system(nefe_ctx* c, const nefe_system_desc* d, int* sys_id) {
     if (rc) return rc;
     if (d->n < 2 || !d->x) return fail(NEFE_EINVAL, "a system needs n >= 2 and positions");
     if (!(d->mass > 0.0)) return fail(NEFE_EINVAL, "mass must be positive");
-    if (d->pot != NEFE_POT_SW && d->pot != NEFE_POT_EINSTEIN) return fail(NEFE_EINVAL, "bad pot");
+    if (d->pot != NEFE_POT_SW && d->pot != NEFE_POT_EINSTEIN && d->pot != NEFE_POT_UF)
+        return fail(NEFE_EINVAL, "bad pot");
     for (int k = 0; k < 3; ++k)
         if (!(d->box[k] > 0.0)) return fail(NEFE_EINVAL, "box must be positive");
     HostSys h;
@@ -537,6 +579,15 @@ int nefe_set_sw_params(nefe_ctx* c, int s, const nefe_sw_params* p) {
     return NEFE_OK;
 }
 
+int nefe_set_uf_params(nefe_ctx* c, int s, const nefe_uf_params* uf) {
+    int rc = check_sys(c, s);
+    if (rc) return rc;
+    if ((rc = not_ready(c, "nefe_set_uf_params"))) return rc;
+    if (!valid_uf(uf)) return fail(NEFE_EINVAL, "UF parameters must be positive and finite");
+    c->sys[s].uf = *uf;
+    return NEFE_OK;
+}
+
 int nefe_set_thermostat(nefe_ctx* c, int s, double T, double damp, uint64_t seed) {
     int rc = check_sys(c, s);
     if (rc) return rc;
@@ -567,7 +618,10 @@ int nefe_set_schedule(nefe_ctx* c, int s, const nefe_schedule* sc) {
     if (!sc || sc->kind < NEFE_SCHED_NONE || sc->kind > NEFE_SCHED_AS) return fail(NEFE_EINVAL, "bad schedule");
     if (sc->kind != NEFE_SCHED_NONE && sc->nsteps < 1) return fail(NEFE_EINVAL, "schedule nsteps must be >= 1");
     if (sc->kind == NEFE_SCHED_RS && !(sc->lambda_f > 0.0)) return fail(NEFE_EINVAL, "lambda_f must be > 0");
-    if (sc->kind == NEFE_SCHED_FL && !(sc->k_E > 0.0)) return fail(NEFE_EINVAL, "k_E must be > 0");
+    if (sc->kind == NEFE_SCHED_FL && sc->ref != NEFE_REF_EINSTEIN && sc->ref != NEFE_REF_UF)
+        return fail(NEFE_EINVAL, "bad FL reference");
+    if (sc->kind == NEFE_SCHED_FL && sc->ref == NEFE_REF_EINSTEIN && !(sc->k_E > 0.0))
+        return fail(NEFE_EINVAL, "k_E must be > 0");
     if (c->sys[s].pair >= 0 && sc->kind != NEFE_SCHED_NONE)
         return fail(NEFE_EINVAL, "systems of a dCCI pair take no schedule");
     c->sys[s].sched = *sc;
@@ -781,7 +835,7 @@ static std::vector<Blob> blobs(nefe_ctx* c) {
     const size_t N = c->ntot;
     const size_t v4 = c->prec == NEFE_FP64 ? sizeof(double4) : sizeof(float4);
     const size_t el = c->prec == NEFE_FP64 ? sizeof(double) : sizeof(float);
-    return {{c->d_st, sizeof(DevState) * c->nsys},
+    std::vector<Blob> all = {{c->d_st, sizeof(DevState) * c->nsys},
             {c->d_acc, sizeof(long long) * c->nsys * ACC_N * kSlots},
             {c->d_pairs, sizeof(DevPair) * std::max<size_t>(1, c->pairs.size())},
             {c->d_x, sizeof(double) * 3 * N},
@@ -799,7 +853,13 @@ static std::vector<Blob> blobs(nefe_ctx* c) {
             {c->d_cell_start, sizeof(int) * (size_t)(c->ncells_total + c->nsys)},
             {c->d_nbr, sizeof(int) * N * (size_t)c->cap},
             {c->d_cnt, sizeof(int) * N},
-            {c->d_trace, sizeof(double) * 9 * (size_t)std::max<long long>(1, c->trace_total)}};
+            {c->d_trace, sizeof(double) * 9 * (size_t)std::max<long long>(1, c->trace_total)},
+            {c->d_uf_nbr, c->d_uf_nbr ? sizeof(int) * N * (size_t)kUfCap : 0},
+            {c->d_uf_cnt, c->d_uf_cnt ? sizeof(int) * N : 0}};
+    std::vector<Blob> out;
+    for (const Blob& b : all)
+        if (b.bytes > 0) out.push_back(b);   // the UF rows exist only in contexts with UF systems
+    return out;
 }
 
 int nefe_save(nefe_ctx* c, const char* path) {

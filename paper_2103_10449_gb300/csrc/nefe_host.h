@@ -68,6 +68,27 @@ inline SWc<T> make_swc(const nefe_sw_params& p) {
 
 bool valid_params(const nefe_sw_params* p);
 
+// Uhlenbeck-Ford constants of a system (mode UF_INT or UF_REF; list radius rc + skin).
+inline void fill_uf(DevSys& d, const nefe_uf_params& uf, double skin, int mode) {
+    const double kT = kB * uf.T;
+    const double R = uf.rc + skin;
+    d.uf_mode = mode;
+    d.uf_pk = uf.p * kT;
+    d.uf_is2 = 1.0 / (uf.sigma * uf.sigma);
+    d.uf_rc2 = uf.rc * uf.rc;
+    d.uf_shift = -d.uf_pk * std::log(-std::expm1(-d.uf_rc2 * d.uf_is2));
+    d.uf_R2 = R * R;
+    d.uf_pk_f = (float)d.uf_pk;
+    d.uf_is2_f = (float)d.uf_is2;
+    d.uf_rc2_f = (float)d.uf_rc2;
+    d.uf_shift_f = (float)d.uf_shift;
+    d.uf_R2_f = (float)d.uf_R2;
+}
+inline bool valid_uf(const nefe_uf_params* u) {
+    return u && u->p > 0.0 && u->sigma > 0.0 && u->T > 0.0 && u->rc > 0.0 && std::isfinite(u->p) &&
+           std::isfinite(u->sigma) && std::isfinite(u->T) && std::isfinite(u->rc);
+}
+
 // Single-system descriptors and scratch for the stateless calls and the adjoint context
 // (stream-ordered allocations, released on the same stream).
 struct Scratch1 {
@@ -108,7 +129,9 @@ struct Scratch1 {
 // NEFE_OK when every box length is positive, finite and at least 2 rcs.
 int check_box(const double box[3], double rcs);
 // Sets up the one-system descriptors, the tile table and (cells) the cell arrays.
-int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap, int prec, bool cells);
+// With uf, the system carries a Uhlenbeck-Ford term as U_int (list radius uf->rc + skin).
+int prepare1(Scratch1& S, int n, const double box[3], double rcs, int ncell_cap, int prec, bool cells,
+             const nefe_uf_params* uf = nullptr, double skin = 0.0);
 // Launch arguments over S for n atoms at FP64 positions x.
 Bufs bufs_of(const Scratch1& S, const double* x, int n);
 

@@ -461,6 +461,10 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     const bool valid = ia < ta.count;
     const int i = ta.first + ia;
     if (!valid) return;                          // whole group leaves together
+    if (S.pot != POT_SW) {                       // no SW term: no SW list (uniform over the block)
+        if (lane == 0) b.cnt[i] = 0;
+        return;
+    }
     const int nx = st.ncell[0], ny = st.ncell[1], nz = st.ncell[2];
     const int cell = b.cell_of[i];
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
@@ -581,6 +585,169 @@ __global__ void __launch_bounds__(kTile) k_nlist(Bufs b) {
             nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cnt_s);
     } else {
         nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, buf, cnt_s);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Uhlenbeck-Ford fluid (the liquid's reference system, Sec. 2.1):
+//   u(r) = -p kT ln(1 - exp(-r^2/sigma^2)) - u(rc),  r < rc.
+// R6 (rebuild): UF pair rows.  One thread per atom walks the 125 cells o in {-2..2}^3 around its
+// own (cells are at least rcs wide and rc + skin <= 2 rcs, so they cover the list radius; with
+// at least 5 cells per axis no cell is visited twice) and appends every j within the list
+// radius (rc + skin, FP32 mirror distance with a relative margin of 1e-5: the list only has
+// to contain every pair that can come within rc before the next rebuild).  Rows are in cell
+// order, not sorted: the force kernel sums in fixed point, so the order does not matter.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__device__ void uflist_tile(const Bufs& b, int tile) {
+    using T4 = typename V4<T>::t;
+    const TileAtom ta = tile_of(b, tile);
+    const DevSys& S = b.sys[ta.sys];
+    if (S.uf_mode == UF_NONE) return;            // uniform over the block
+    DevState& st = b.st[ta.sys];
+    if ((int)threadIdx.x >= ta.count) return;
+    const int i = ta.first + threadIdx.x;
+    const int nx = st.ncell[0], ny = st.ncell[1], nz = st.ncell[2];
+    if (nx < 5 || ny < 5 || nz < 5) {
+        b.uf_cnt[i] = 0;
+        atomicOr(&st.err, NEFE_ERR_BOX);
+        return;
+    }
+    const int cell = b.cell_of[i];
+    const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+    const int* start = b.cell_start + S.cell0 + ta.sys;
+    const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
+    const T hx = pick<T>(st.h[0], st.h_f[0]), hy = pick<T>(st.h[1], st.h_f[1]), hz = pick<T>(st.h[2], st.h_f[2]);
+    const T R2 = pick<T>(S.uf_R2 * (1.0 + 1e-5), S.uf_R2_f * (1.0f + 1e-5f));
+    const T4* xc = reinterpret_cast<const T4*>(b.xcs) + S.off;
+    int* row = b.uf_nbr + (size_t)i * kUfCap;
+    int count = 0;
+    for (int oz = -2; oz <= 2; ++oz) {
+        int zz = cz + oz;
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        for (int oy = -2; oy <= 2; ++oy) {
+            int yy = cy + oy;
+            yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+            for (int ox = -2; ox <= 2; ++ox) {
+                int xx = cx + ox;
+                xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+                const int c2 = xx + nx * (yy + ny * zz);
+                const int lo = max(0, min(start[c2], S.n)), hi = max(lo, min(start[c2 + 1], S.n));
+                const T offx = (T)ox * hx, offy = (T)oy * hy, offz = (T)oz * hz;
+                const unsigned code = (unsigned)((ox + 2) + 5 * (oy + 2) + 25 * (oz + 2));
+                for (int q = lo; q < hi; ++q) {
+                    const T4 xj = xc[q];
+                    const int j = unpack_index(xj.w);
+                    if (j < S.off || j >= S.off + S.n) {
+                        atomicOr(&st.err, NEFE_ERR_CELL);
+                        continue;
+                    }
+                    if (j == i) continue;
+                    const T dx = xj.x - xi.x + offx, dy = xj.y - xi.y + offy, dz = xj.z - xi.z + offz;
+                    if (dx * dx + dy * dy + dz * dz < R2) {
+                        if (count < kUfCap) row[count] = (int)((unsigned)j | (code << kUfShift));
+                        ++count;
+                    }
+                }
+            }
+        }
+    }
+    b.uf_cnt[i] = count;
+    if (count > kUfCap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
+}
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_uflist(Bufs b) {
+    NEFE_FOR_TILES(b, uflist_tile<T>(b, tile));
+}
+
+// Fixed-point accumulation of the UF pair sums (order independent, so the unsorted rows give
+// bitwise reproducible forces): 2^-32 units in the FP32 kernel, 2^-40 in the FP64 kernel.
+template <typename T> struct UfFix;
+template <> struct UfFix<float> {
+    __device__ static long long to(float v) { return __float2ll_rn(v * 4294967296.0f); }
+    __device__ static float from(long long q) { return (float)((double)q * 0x1p-32); }
+};
+template <> struct UfFix<double> {
+    __device__ static long long to(double v) { return __double2ll_rn(v * 0x1p40); }
+    __device__ static double from(long long q) { return (double)q * 0x1p-40; }
+};
+__device__ __forceinline__ float xexpm1(float v) { return expm1f(v); }
+__device__ __forceinline__ double xexpm1(double v) { return ::expm1(v); }
+__device__ __forceinline__ float xlogf_acc(float v) { return logf(v); }
+__device__ __forceinline__ double xlogf_acc(double v) { return ::log(v); }
+
+// Per step (or stateless): UF force and energy of each atom of a UF system from its row.
+// Each pair is seen from both ends: half its energy and virial per end, the full force.
+// The energy goes to U_int (pot = UF) or to the FL reference energy U_E (UF reference); the
+// virial enters the pressure only when the UF term is U_int.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kTile) k_uf(Bufs b) {
+    using T4 = typename V4<T>::t;
+    __shared__ T4 soff[125];
+    const int tile = b.uf_tiles ? b.uf_tiles[blockIdx.x] : (int)blockIdx.x;
+    const TileAtom ta = tile_of(b, tile);
+    const DevSys& S = b.sys[ta.sys];
+    DevState& st = b.st[ta.sys];
+    if (S.uf_mode == UF_NONE) return;            // uniform over the block
+    if (threadIdx.x < 125) {
+        const int c = threadIdx.x;
+        const int ox = c % 5 - 2, oy = (c / 5) % 5 - 2, oz = c / 25 - 2;
+        soff[c] = mk4((T)ox * pick<T>(st.h[0], st.h_f[0]), (T)oy * pick<T>(st.h[1], st.h_f[1]),
+                      (T)oz * pick<T>(st.h[2], st.h_f[2]), (T)0);
+    }
+    __syncthreads();
+    const T pk = pick<T>(S.uf_pk, S.uf_pk_f), is2 = pick<T>(S.uf_is2, S.uf_is2_f);
+    const T rc2 = pick<T>(S.uf_rc2, S.uf_rc2_f), shift = pick<T>(S.uf_shift, S.uf_shift_f);
+    long long q[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // f xyz, energy, virial xx yy zz xy xz yz
+    const bool valid = (int)threadIdx.x < ta.count;
+    const int i = ta.first + threadIdx.x;
+    if (valid) {
+        const T4* X = reinterpret_cast<const T4*>(b.xs);
+        const T4 xi = X[i];
+        const int cnt = min(b.uf_cnt[i], kUfCap);
+        const int* row = b.uf_nbr + (size_t)i * kUfCap;
+        for (int a = 0; a < cnt; ++a) {
+            const unsigned e = (unsigned)row[a];
+            const T4 xj = X[e & kUfMask];
+            const T4 oh = soff[e >> kUfShift];
+            const T dx = (xj.x - xi.x) + oh.x, dy = (xj.y - xi.y) + oh.y, dz = (xj.z - xi.z) + oh.z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < rc2)) continue;
+            const T xx = r2 * is2;
+            const T u = -pk * xlogf_acc(-xexpm1(-xx)) - shift;
+            const T c = (T)2 * pk * is2 / xexpm1(xx);      // force on j along d: c d; on i: -c d
+            const T hc = (T)0.5 * c;
+            q[0] += UfFix<T>::to(-c * dx);
+            q[1] += UfFix<T>::to(-c * dy);
+            q[2] += UfFix<T>::to(-c * dz);
+            q[3] += UfFix<T>::to((T)0.5 * u);
+            q[4] += UfFix<T>::to(hc * dx * dx);
+            q[5] += UfFix<T>::to(hc * dy * dy);
+            q[6] += UfFix<T>::to(hc * dz * dz);
+            q[7] += UfFix<T>::to(hc * dx * dy);
+            q[8] += UfFix<T>::to(hc * dx * dz);
+            q[9] += UfFix<T>::to(hc * dy * dz);
+        }
+    }
+    T v[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = UfFix<T>::from(q[k]);
+    if (valid) {
+        if (MODE == FM_FORCES) {
+            const size_t N = b.ntot;
+            b.f_out[i] = (double)v[0]; b.f_out[N + i] = (double)v[1]; b.f_out[2 * N + i] = (double)v[2];
+            if (b.e_atom) b.e_atom[i] = (double)v[3];
+        } else {
+            reinterpret_cast<T4*>(b.uf_F)[i] = mk4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    long long* acc = b.acc + (size_t)ta.sys * ACC_N * kSlots;
+    if (S.uf_mode == UF_INT) {
+        T red[8] = {v[3], (T)0, v[4], v[5], v[6], v[7], v[8], v[9]};   // U_int, (U_E), virial
+        block_sum_to_acc<T, 8>(red, acc, ACC_UINT, &st.err);
+    } else {
+        T red[1] = {v[3]};
+        block_sum_to_acc<T, 1>(red, acc, ACC_UREF, &st.err);
     }
 }
 
@@ -1225,6 +1392,11 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                     u_ref = (T)0.5 * k_e * d2;
                     for (int k = 0; k < 3; ++k) fe[k] = -k_e * d[k];
                 }
+                if (S.uf_mode != UF_NONE) {     // UF force of this step (its energy is summed by k_uf)
+                    const T4 fu = reinterpret_cast<const T4*>(b.uf_F)[i];
+                    T* dst = S.uf_mode == UF_INT ? fint : fe;
+                    dst[0] = fu.x; dst[1] = fu.y; dst[2] = fu.z;
+                }
                 T* V = reinterpret_cast<T*>(b.v);
                 T v[3] = {pv[0], pv[1], pv[2]};
                 const T si = pick<T>(st.scale_int, st.scale_int_f), se = pick<T>(st.scale_E, st.scale_E_f);
@@ -1616,6 +1788,26 @@ void launch_decode_grad(const long long* acc, double* out8, cudaStream_t s) {
 
 void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s) {
     k_decode_ev<<<1, 32, 0, s>>>(acc, out7);
+}
+
+void launch_uf_list(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches) {
+    if (ntiles <= 0 || !b.uf_nbr) return;
+    const int g = rebuild_grid(b, ntiles);
+    if (precision == NEFE_FP64) k_uflist<double><<<g, kTile, 0, s>>>(b);
+    else k_uflist<float><<<g, kTile, 0, s>>>(b);
+    if (launches) *launches += 1;
+}
+
+void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {
+    if (ntiles <= 0 || !b.uf_nbr) return;
+    if (precision == NEFE_FP64) {
+        if (mode == FM_FORCES) k_uf<double, FM_FORCES><<<ntiles, kTile, 0, s>>>(b);
+        else k_uf<double, FM_STEP><<<ntiles, kTile, 0, s>>>(b);
+    } else {
+        if (mode == FM_FORCES) k_uf<float, FM_FORCES><<<ntiles, kTile, 0, s>>>(b);
+        else k_uf<float, FM_STEP><<<ntiles, kTile, 0, s>>>(b);
+    }
+    if (launches) *launches += 1;
 }
 
 void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {

@@ -51,6 +51,10 @@ struct Bufs {
     double* e_atom;          // stateless: per-atom energy (may be NULL)
     int want_grad;           // pass A also sums dE/d(A, B, p, q, a, lambda3, gamma)
     int list_lanes;          // lanes per atom of the list build (8, 16 or 32; 0: 8)
+    int* uf_nbr;             // [ntot][kUfCap] Uhlenbeck-Ford pair rows (NULL: no UF system)
+    int* uf_cnt;             // [ntot] their lengths
+    void* uf_F;              // [ntot] UF force and atom energy of the step (T4)
+    const int* uf_tiles;     // tiles of the UF systems (per-step UF kernel), or NULL: every tile
 };
 
 enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };
@@ -68,6 +72,12 @@ void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, i
 // Half kick + drift + mirror + displacement check + noise sums (mode 0: no kick/drift).
 void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s,
                        long* launches);
+// Uhlenbeck-Ford pair rows of the UF systems (after the cell fill; flagged systems only when a
+// rebuild worklist is set).
+void launch_uf_list(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches);
+// Uhlenbeck-Ford forces and energies over `ntiles` tiles (b.uf_tiles, or every tile when NULL);
+// mode FM_FORCES writes b.f_out / b.e_atom (stateless), otherwise b.uf_F for pass B.
+void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches);
 // Force pass A (edges: pair terms, triplets centred on each atom, leg forces per edge).
 void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
                   long* launches);

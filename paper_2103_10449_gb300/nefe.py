@@ -18,7 +18,9 @@ NEFE_OK, NEFE_EINVAL, NEFE_ENOMEM, NEFE_ECUDA, NEFE_EOVERFLOW = 0, -1, -2, -3, -
 NEFE_ENAN, NEFE_EDEGEN, NEFE_ETIMEOUT, NEFE_ESTATE = -6, -7, -8, -9
 NEFE_ERR_NBR_OVERFLOW, NEFE_ERR_SHELL_OVERFLOW, NEFE_ERR_NAN, NEFE_ERR_DEGEN, NEFE_ERR_BOX = 1, 2, 4, 8, 16
 NEFE_FP32, NEFE_FP64 = 0, 1
-NEFE_POT_SW, NEFE_POT_EINSTEIN = 0, 1
+NEFE_POT_SW, NEFE_POT_EINSTEIN, NEFE_POT_UF = 0, 1, 2
+NEFE_REF_EINSTEIN, NEFE_REF_UF = 0, 1
+NEFE_UF_CAP = 256
 NEFE_BARO_NONE, NEFE_BARO_ISO, NEFE_BARO_ANISO = 0, 1, 2
 NEFE_SCHED_NONE, NEFE_SCHED_FL, NEFE_SCHED_RS, NEFE_SCHED_AS = 0, 1, 2, 3
 NEFE_DCCI_TEMP, NEFE_DCCI_PRESS = 0, 1
@@ -37,6 +39,10 @@ class nefe_sw_params(ctypes.Structure):
                                                "gamma", "cos0")]
 
 
+class nefe_uf_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("p", "sigma", "T", "rc")]
+
+
 class nefe_system_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("x", ctypes.POINTER(ctypes.c_double)),
                 ("v", ctypes.POINTER(ctypes.c_double)), ("r0", ctypes.POINTER(ctypes.c_double)),
@@ -47,7 +53,8 @@ class nefe_system_desc(ctypes.Structure):
 class nefe_schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("direction", ctypes.c_int), ("nsteps", ctypes.c_long),
                 ("k_E", ctypes.c_double), ("lambda_f", ctypes.c_double), ("P_GPa", ctypes.c_double),
-                ("P0_GPa", ctypes.c_double), ("P1_GPa", ctypes.c_double), ("lambda0", ctypes.c_double)]
+                ("P0_GPa", ctypes.c_double), ("P1_GPa", ctypes.c_double), ("lambda0", ctypes.c_double),
+                ("ref", ctypes.c_int)]
 
 
 class nefe_adjoint_desc(ctypes.Structure):
@@ -92,6 +99,9 @@ SIGNATURES = {
     "nefe_neighbor_build": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, ctypes.c_int, _vp, _vp, _c_int_p, _vp],
     "nefe_sw_forces": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
                        ctypes.POINTER(nefe_sw_params), ctypes.c_int, _vp, _vp, _vp, _c_int_p, _vp],
+    "nefe_uf_forces": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, ctypes.c_double,
+                       ctypes.POINTER(nefe_uf_params), ctypes.c_int, _vp, _vp, _vp, _vp],
+    "nefe_set_uf_params": [_vp, ctypes.c_int, ctypes.POINTER(nefe_uf_params)],
     "nefe_sw_energy_grad": [_vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
                             ctypes.POINTER(nefe_sw_params), ctypes.c_int, _vp, _vp, _vp],
     "nefe_sw_dual": [_vp, _vp, ctypes.c_int, _c_dbl_p, ctypes.c_double, _vp, _vp, ctypes.c_int,
@@ -242,6 +252,15 @@ def nefe_sw_forces(x, n, box, rcs, nbr, cnt, cap, prm, precision, f, e_atom=None
     return ovf.value
 
 
+def uf_params(p=25.0, sigma=2.0, T=2200.0, rc=8.0) -> nefe_uf_params:
+    return nefe_uf_params(float(p), float(sigma), float(T), float(rc))
+
+
+def nefe_uf_forces(x, n, box, rcs, skin, uf, precision, f, e_atom=None, energy_virial=None, stream=None):
+    _check(load().nefe_uf_forces(_ptr(x), int(n), _box(box), float(rcs), float(skin), ctypes.byref(uf),
+                                 int(precision), _ptr(f), _ptr(e_atom), _ptr(energy_virial), _stream(stream)))
+
+
 def nefe_sw_energy_grad(x, n, box, rcs, nbr, cnt, cap, prm, precision, f, energy_grad, stream=None):
     _check(load().nefe_sw_energy_grad(_ptr(x), int(n), _box(box), float(rcs), _ptr(nbr), _ptr(cnt), int(cap),
                                       ctypes.byref(prm), int(precision), _ptr(f), _ptr(energy_grad),
@@ -303,6 +322,9 @@ class Context:
     def set_sw_params(self, sys, prm):
         _check(self._L.nefe_set_sw_params(self.h, int(sys), ctypes.byref(prm)))
 
+    def set_uf_params(self, sys, uf):
+        _check(self._L.nefe_set_uf_params(self.h, int(sys), ctypes.byref(uf)))
+
     def set_thermostat(self, sys, T, damp, seed):
         _check(self._L.nefe_set_thermostat(self.h, int(sys), float(T), float(damp), int(seed)))
 
@@ -310,9 +332,9 @@ class Context:
         _check(self._L.nefe_set_barostat(self.h, int(sys), int(mode), float(P_GPa), float(pdamp)))
 
     def set_schedule(self, sys, kind, direction=1, nsteps=1, k_E=0.0, lambda_f=1.0, P_GPa=0.0, P0_GPa=0.0,
-                     P1_GPa=0.0, lambda0=1.0):
+                     P1_GPa=0.0, lambda0=1.0, ref=NEFE_REF_EINSTEIN):
         s = nefe_schedule(kind=kind, direction=direction, nsteps=nsteps, k_E=k_E, lambda_f=lambda_f, P_GPa=P_GPa,
-                          P0_GPa=P0_GPa, P1_GPa=P1_GPa, lambda0=lambda0)
+                          P0_GPa=P0_GPa, P1_GPa=P1_GPa, lambda0=lambda0, ref=ref)
         _check(self._L.nefe_set_schedule(self.h, int(sys), ctypes.byref(s)))
 
     def pair_dcci(self, a, b, T0, P0_GPa, mode, frm, to, nsteps):
