@@ -160,12 +160,25 @@ def test_ideal_gas_to_uf_free_energy_follows_the_virial_series_on_gpu(N):
     rho = target / b2
     L = (n / rho) ** (1.0 / 3.0)
     box = np.array([L, L, L])
+    # backward switches start from the UF fluid equilibrated at lambda = 1 (2 ps at 2200 K)
+    eq = N.Context(precision=N.NEFE_FP32, skin=SKIN, nbr_cap=48)
+    for r in range(reps):
+        x = np.random.default_rng(800 + r).uniform(0.0, L, (n, 3))
+        s = eq.add_system(x, box, v=I.gaussian_velocities(n, _sv(T), 900 + r), pot=N.NEFE_POT_UF)
+        eq.set_uf_params(s, N.uf_params(*UF))
+        eq.set_thermostat(s, T, 0.1, 950 + r)
+    eq.run(2000)
+    uf_states = [eq.get_state(s)[:2] for s in range(reps)]
+    eq.close()
     ctx = N.Context(precision=N.NEFE_FP32, skin=SKIN, nbr_cap=48)
     fw, bw = [], []
     for r in range(2 * reps):
-        x = np.random.default_rng(500 + r).uniform(0.0, L, (n, 3))
-        s = ctx.add_system(x, box, v=I.gaussian_velocities(n, _sv(T), 600 + r), r0=x, pot=N.NEFE_POT_EINSTEIN,
-                           k_int=0.0)
+        if r < reps:       # the ideal gas: uniform positions are its equilibrium
+            x = np.random.default_rng(500 + r).uniform(0.0, L, (n, 3))
+            v = I.gaussian_velocities(n, _sv(T), 600 + r)
+        else:
+            x, v = uf_states[r - reps]
+        s = ctx.add_system(x, box, v=v, r0=x, pot=N.NEFE_POT_EINSTEIN, k_int=0.0)
         ctx.set_uf_params(s, N.uf_params(*UF))
         ctx.set_thermostat(s, T, 0.1, 700 + r)
         fwd = r < reps
