@@ -70,6 +70,7 @@ struct nefe_ctx {
     void *d_shd = nullptr, *d_P = nullptr, *d_spill = nullptr;
     int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr;
     int *d_uf_nbr = nullptr, *d_uf_cnt = nullptr, *d_uf_tiles = nullptr;
+    int* d_lacc = nullptr;   // scatter-form force accumulators (FP32 contexts)
     void* d_uf_F = nullptr;
     int n_uf_tiles = 0;      // tiles of the systems with a Uhlenbeck-Ford term
     int4* d_q = nullptr;
@@ -80,7 +81,8 @@ struct nefe_ctx {
     DevGroup* d_groups = nullptr;
     double* d_trace = nullptr;
     std::vector<void*> allocs;
-    int lanes = 8;           // pass A lanes per atom (1 = one thread per atom, 4, 8, 16, 32)
+    int lanes = 8;           // pass A lanes per atom (1 = one thread per atom, 4, 8, 16, 32; 0 = one
+                             // thread per atom in the scatter form, whose pass B is k_finish)
     int glanes = 4;          // pass B lanes per atom (1, 2, 4, 8)
     int llanes = 8;          // list-build lanes per atom (8, 16, 32)
     double tune_us = 0.0;
@@ -167,7 +169,7 @@ void enqueue_forces(nefe_ctx* c, int mode, int slot = -1) {
         if (prof) cudaEventRecordWithFlags(c->ev0[e], c->stream, cudaEventRecordExternal);
         launch_edges(b, c->prec, c->lanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
         if (prof) cudaEventRecordWithFlags(c->ev1[e], c->stream, cudaEventRecordExternal);
-        launch_gather(b, c->prec, c->glanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
+        launch_gather(b, c->prec, c->lanes == 0 ? 0 : c->glanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
         if (prof) cudaEventRecordWithFlags(c->ev2[e], c->stream, cudaEventRecordExternal);
     }
 }
@@ -211,6 +213,7 @@ void fill_results(const DevSys& S, const DevState& st, nefe_results* out) {
 // Lists, mirror and total forces from the current x, v (lambda and scales unchanged).
 int resetup(nefe_ctx* c) {
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * (size_t)c->nsys * ACC_N * kSlots, c->stream));
+    if (c->d_lacc) NEFE_CU(cudaMemsetAsync(c->d_lacc, 0, 4 * sizeof(int) * (size_t)c->ntot, c->stream));
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 1, c->stream, &c->launches);
     if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
     launch_kick_drift(c->b, c->prec, c->ntiles, 0, c->stream, &c->launches);
@@ -398,6 +401,10 @@ int setup(nefe_ctx* c) {
     if ((rc = dalloc(c, &c->d_shj, sizeof(int) * N * (size_t)kShell))) return rc;
     if ((rc = dalloc(c, &c->d_shn, sizeof(int) * N))) return rc;
     if ((rc = dalloc(c, &c->d_P, 3 * v4 * N))) return rc;
+    if (c->prec == NEFE_FP32) {
+        if ((rc = dalloc(c, &c->d_lacc, 4 * sizeof(int) * N))) return rc;
+        NEFE_CU(cudaMemset(c->d_lacc, 0, 4 * sizeof(int) * N));
+    }
     if ((rc = dalloc(c, &c->d_rtiles, sizeof(int) * tile_sys.size()))) return rc;
     if ((rc = dalloc(c, &c->d_rcount, sizeof(int)))) return rc;
     if ((rc = dalloc(c, &c->d_q, sizeof(int4) * N))) return rc;
@@ -473,6 +480,7 @@ int setup(nefe_ctx* c) {
     b.trace = c->d_trace;
     b.list_lanes = c->llanes;
     b.uf_nbr = c->d_uf_nbr; b.uf_cnt = c->d_uf_cnt; b.uf_F = c->d_uf_F; b.uf_tiles = c->d_uf_tiles;
+    b.lacc = c->d_lacc;
 
     launch_inject(b, c->prec, c->ntiles, nullptr, c->d_vtmp, c->stream);
     NEFE_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * nsys * ACC_N * kSlots, c->stream));
@@ -946,6 +954,7 @@ static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>
     int rc = NEFE_OK;
     for (size_t ka = 0; ka < ranked_a.size() && ka < 2 && rc == NEFE_OK; ++ka) {
         for (int lb : {1, 2, 4, 8}) {
+            if (ranked_a[ka].second == 0 && lb != 1) continue;   // the scatter form has one pass B
             c->lanes = ranked_a[ka].second;
             c->glanes = lb;
             drop_graph(c);
@@ -1024,18 +1033,41 @@ int nefe_autotune(nefe_ctx* c) {
         }
         return best_trial;
     };
-    const int cand[5] = {1, 4, 8, 16, 32};
+    const int cand[6] = {0, 1, 4, 8, 16, 32};
     double best = 1e30;
     int best_l = c->lanes;
     std::vector<std::pair<double, int>> ranked_a;   // (time, lanes) of every pass-A variant
+    // the scatter form's pass A is timed together with its pass B (k_finish, which clears the
+    // accumulators); the gather form's pass B is timed below
+    const size_t el_ = c->prec == NEFE_FP64 ? sizeof(double) : sizeof(float);
+    void *tv0 = nullptr, *tf0 = nullptr;
+    NEFE_CU(cudaMalloc(&tv0, el_ * 3 * c->ntot));
+    NEFE_CU(cudaMalloc(&tf0, 4 * el_ * c->ntot));
+    NEFE_CU(cudaMemcpyAsync(tv0, c->d_v, el_ * 3 * c->ntot, cudaMemcpyDeviceToDevice, c->stream));
+    Bufs b0 = b;
+    b0.v = tv0;
+    b0.F = tf0;
+    double scatter_us = 1e30;
     for (int l : cand) {
-        if (c->prec == NEFE_FP64 && (l == 1 || l == 4)) continue;
-        const double us = time_us([&] { launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches); });
+        if (c->prec == NEFE_FP64 && (l == 0 || l == 1 || l == 4)) continue;
+        double us;
+        if (l == 0) {
+            us = time_us([&] {
+                launch_edges(b0, c->prec, 0, c->ntiles, FM_FORCES, c->stream, &c->launches);
+                launch_gather(b0, c->prec, 0, c->ntiles, FM_STEP, c->stream, &c->launches);
+            });
+            scatter_us = us;
+        } else {
+            us = time_us([&] { launch_edges(b, c->prec, l, c->ntiles, FM_FORCES, c->stream, &c->launches); });
+        }
         ranked_a.push_back({us, l});
         if (us < best) { best = us; best_l = l; }
     }
+    NEFE_CU(cudaStreamSynchronize(c->stream));
+    cudaFree(tv0);
+    cudaFree(tf0);
     std::sort(ranked_a.begin(), ranked_a.end());
-    launch_edges(b, c->prec, best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
+    launch_edges(b, c->prec, best_l == 0 ? 1 : best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
     double best_g = 1e30;
     int best_gl = c->glanes;
     {
@@ -1050,15 +1082,23 @@ int nefe_autotune(nefe_ctx* c) {
         Bufs bs = b;
         bs.v = tv;
         bs.F = tf;
-        // each variant right after pass A, as in a step (pass B reads what pass A just wrote)
+        // each variant right after pass A, as in a step (pass B reads what pass A just wrote);
+        // the scatter form was timed with its own pass B above
+        const int la = best_l == 0 ? 1 : best_l;
+        double base_a = best;
+        for (const auto& r : ranked_a)
+            if (r.second == la) base_a = r.first;
         for (int l : {1, 2, 4, 8}) {
             const double us = time_us([&] {
-                launch_edges(b, c->prec, best_l, c->ntiles, FM_FORCES, c->stream, &c->launches);
+                launch_edges(b, c->prec, la, c->ntiles, FM_FORCES, c->stream, &c->launches);
                 launch_gather(bs, c->prec, l, c->ntiles, FM_STEP, c->stream, &c->launches);
             });
             if (us < best_g) { best_g = us; best_gl = l; }
         }
-        best_g -= best;
+        best_g -= base_a;
+        // a gather-form pair faster than the scatter form (pass A + its pass B) replaces it
+        if (best_l == 0 && base_a + best_g < scatter_us) best_l = la;
+        if (best_l == 0) best_g = 0.0;
         NEFE_CU(cudaStreamSynchronize(c->stream));
         cudaFree(tv);
         cudaFree(tf);
@@ -1095,7 +1135,7 @@ int nefe_get_tuning(nefe_ctx* c, int* lanes, double* best_us) {
 
 int nefe_set_tuning(nefe_ctx* c, int lanes) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
-    if (!lanes_supported(lanes) || (c->prec == NEFE_FP64 && (lanes == 1 || lanes == 4)))
+    if (!lanes_supported(lanes) || (c->prec == NEFE_FP64 && (lanes == 0 || lanes == 1 || lanes == 4)))
         return fail(NEFE_EINVAL, "unsupported lanes per atom %d", lanes);
     if (lanes != c->lanes) drop_graph(c);
     c->lanes = lanes;

@@ -1112,7 +1112,27 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
 constexpr int kShell1Shared = 8;
 constexpr int kShell1 = kShell1Shared + kSpill1;
 constexpr int kEdges1Threads = 64;
-template <typename T>
+
+// Scatter form of the force passes: pass A adds every leg force (and the atom's own force)
+// into per-atom int32 accumulators (units of 2^-21 eV/A) with global reductions.  Integer
+// addition is associative, so the result does not depend on the order in which the
+// reductions arrive (bitwise reproducible), and no second pass has to find the legs again:
+// a streaming epilogue (k_finish) reads and clears each atom's accumulator.  A term is
+// rounded to 2^-22 eV/A; one above kLegLimit eV/A (whose sum over the terms an atom can
+// receive could overflow int32) is dropped and flags the system.
+constexpr float kLegScale = 2097152.0f;          // 2^21
+constexpr float kLegLimit = 48.0f;
+__device__ __forceinline__ void red_force(int* acc4, float x, float y, float z, unsigned* err) {
+    if (!(fabsf(x) < kLegLimit && fabsf(y) < kLegLimit && fabsf(z) < kLegLimit)) {
+        atomicOr(err, NEFE_ERR_NAN);
+        return;
+    }
+    atomicAdd(acc4 + 0, __float2int_rn(x * kLegScale));
+    atomicAdd(acc4 + 1, __float2int_rn(y * kLegScale));
+    atomicAdd(acc4 + 2, __float2int_rn(z * kLegScale));
+}
+
+template <typename T, bool SCATTER>
 __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
@@ -1130,7 +1150,8 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
     const int t = threadIdx.x;
     const int ia = part * NT + t;
-    if (ia >= ta.count) return;
+    T red8[8] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};   // scatter form: energy, -, virial
+    if (ia < ta.count) {
     const int i = ta.first + ia;
     const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
     const int ci = min(b.cnt[i], b.cap);
@@ -1224,7 +1245,8 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
             eh += dc * s1;
         }
         const T lx = cc * ua.x - ax, ly = cc * ua.y - ay, lz = cc * ua.z - az;
-        Fl[a] = mk4(lx, ly, lz, (T)0);
+        if constexpr (SCATTER) red_force(b.lacc + 4 * (size_t)Sj[a], lx, ly, lz, &st.err);
+        else Fl[a] = mk4(lx, ly, lz, (T)0);
         fx -= lx; fy -= ly; fz -= lz;
         en += (T)0.5 * P.epslam * ga * eh;
         const T dx = ua.x * ra, dy = ua.y * ra, dz = ua.z * ra;
@@ -1233,11 +1255,20 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
         w4 += (T)0.5 * (dx * lz + dz * lx);
         w5 += (T)0.5 * (dy * lz + dz * ly);
     }
-    T4* Pa = reinterpret_cast<T4*>(b.P);
-    Pa[i] = mk4(fx, fy, fz, en);
-    Pa[b.ntot + 2 * (size_t)i] = mk4(w0, w1, w2, w3);
-    Pa[b.ntot + 2 * (size_t)i + 1] = mk4(w4, w5, (T)0, (T)0);
+    if constexpr (SCATTER) {
+        red_force(b.lacc + 4 * (size_t)i, fx, fy, fz, &st.err);
+        if (b.e_atom) b.e_atom[i] = (double)en;
+        red8[0] = en;
+        red8[2] = w0; red8[3] = w1; red8[4] = w2; red8[5] = w3; red8[6] = w4; red8[7] = w5;
+    } else {
+        T4* Pa = reinterpret_cast<T4*>(b.P);
+        Pa[i] = mk4(fx, fy, fz, en);
+        Pa[b.ntot + 2 * (size_t)i] = mk4(w0, w1, w2, w3);
+        Pa[b.ntot + 2 * (size_t)i + 1] = mk4(w4, w5, (T)0, (T)0);
+    }
     b.shn[i] = m;
+    }   // ia < ta.count
+    if constexpr (SCATTER) block_sum_to_acc<T, 8>(red8, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
 
 // Force pass B, L lanes per atom:
@@ -1247,6 +1278,13 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
 // symmetric because both ends compute the same r^2 bit for bit).  Then, in FM_SETUP /
 // FM_STEP: Einstein springs, lambda mixing, Langevin force (this step's noise with its
 // per-system mean removed), second half kick and the kinetic sums.
+template <typename T, int MODE>
+__device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
+                                            const T (&f)[3], T e_i, bool write_e, const T (&pd)[3],
+                                            const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14]);
+template <typename T>
+__device__ __forceinline__ void noise_mean(const Bufs& b, const DevSys& S, int sys, T* s_xm);
+
 template <typename T, int MODE, int L>
 __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     using T4 = typename V4<T>::t;
@@ -1256,18 +1294,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
     __shared__ T s_xm[3];
-    if (MODE != FM_FORCES && threadIdx.x < 3) {
-        const long long* acc = b.acc + (size_t)ta.sys * ACC_N * kSlots + (size_t)(ACC_XI + threadIdx.x) * kSlots;
-        long long sum = 0;
-        for (int sl = 0; sl < kSlots; ++sl) sum += acc[sl];
-        if constexpr (sizeof(T) == 4) {   // sum 2^-32 / n from its 32-bit halves, FP32 only
-            const float hi = (float)(int)(sum >> 32);
-            const float lo = (float)(unsigned)(sum & 0xffffffffLL) * 0x1p-32f;
-            s_xm[threadIdx.x] = (hi + lo) * S.inv_n_f;
-        } else {
-            s_xm[threadIdx.x] = (T)((double)sum / kFix / (double)S.n);
-        }
-    }
+    if (MODE != FM_FORCES) noise_mean<T>(b, S, ta.sys, s_xm);
     __syncthreads();
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
@@ -1373,10 +1400,24 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 red[2] = wa.x; red[3] = wa.y; red[4] = wa.z; red[5] = wa.w; red[6] = wb.x; red[7] = wb.y;
             }
         }
-        if (lane == 0) {
+        if (lane == 0) finish_atom<T, MODE>(b, S, st, i, f, e_i, true, pd, pv, pz, s_xm, red);
+    }
+    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+}
+
+// The epilogue of force pass B for atom i with SW (or zero) force f: the stateless output, or
+// Einstein springs / UF force, lambda mixing, Langevin force with the per-system mean of this
+// step's noise removed, second half kick, total force for the next step and the kinetic sums.
+// pd: spring offset x - r0; pv: velocity; pz: noise of the step; s_xm: the per-system noise mean.
+template <typename T, int MODE>
+__device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
+                                            const T (&f)[3], T e_i, bool write_e, const T (&pd)[3],
+                                            const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14]) {
+    using T4 = typename V4<T>::t;
+    const size_t N = b.ntot;
             if (MODE == FM_FORCES) {
                 b.f_out[i] = (double)f[0]; b.f_out[N + i] = (double)f[1]; b.f_out[2 * N + i] = (double)f[2];
-                if (b.e_atom) b.e_atom[i] = (double)e_i;
+                if (b.e_atom && write_e) b.e_atom[i] = (double)e_i;
             } else {
                 T fint[3] = {f[0], f[1], f[2]}, fe[3] = {(T)0, (T)0, (T)0};
                 T u_int = 0, u_ref = 0;
@@ -1422,7 +1463,73 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 red[12] = me * v[0] * v[2];
                 red[13] = me * v[1] * v[2];
             }
+}
+
+// Per-system mean of this step's thermostat noise (the "zero yes" removal), from the
+// fixed-point sums of k_kick_drift, into s_xm[3].  Threads 0..2 write; the caller syncs.
+template <typename T>
+__device__ __forceinline__ void noise_mean(const Bufs& b, const DevSys& S, int sys, T* s_xm) {
+    if (threadIdx.x < 3) {
+        const long long* acc = b.acc + (size_t)sys * ACC_N * kSlots + (size_t)(ACC_XI + threadIdx.x) * kSlots;
+        long long sum = 0;
+        for (int sl = 0; sl < kSlots; ++sl) sum += acc[sl];
+        if constexpr (sizeof(T) == 4) {   // sum 2^-32 / n from its 32-bit halves, FP32 only
+            const float hi = (float)(int)(sum >> 32);
+            const float lo = (float)(unsigned)(sum & 0xffffffffLL) * 0x1p-32f;
+            s_xm[threadIdx.x] = (hi + lo) * S.inv_n_f;
+        } else {
+            s_xm[threadIdx.x] = (T)((double)sum / kFix / (double)S.n);
         }
+    }
+}
+
+// Force pass B of the scatter form: one thread per atom reads and clears the atom's force
+// accumulator (the pair, own-triplet and leg forces pass A added) and runs the epilogue.  The
+// SW energy and virial were summed by pass A.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
+    using T4 = typename V4<T>::t;
+    const int tile = blockIdx.x + b.tile_base;
+    const TileAtom ta = tile_of(b, tile);
+    const DevSys& S = b.sys[ta.sys];
+    DevState& st = b.st[ta.sys];
+    __shared__ T s_xm[3];
+    if (MODE != FM_FORCES) noise_mean<T>(b, S, ta.sys, s_xm);
+    __syncthreads();
+    T red[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) red[k] = (T)0;
+    if ((int)threadIdx.x < ta.count) {
+        const int i = ta.first + threadIdx.x;
+        const size_t N = b.ntot;
+        T pd[3] = {(T)0, (T)0, (T)0}, pv[3] = {(T)0, (T)0, (T)0}, pz[3] = {(T)0, (T)0, (T)0};
+        if (MODE != FM_FORCES) {
+            if (S.springs) {
+                const T4 d0 = reinterpret_cast<const T4*>(b.sd0)[i];
+                const T* DH = reinterpret_cast<const T*>(b.dhi);
+                const T* DL = reinterpret_cast<const T*>(b.dlo);
+                pd[0] = d0.x; pd[1] = d0.y; pd[2] = d0.z;
+                for (int k = 0; k < 3; ++k) {
+                    pd[k] += DH[k * N + i];
+                    if constexpr (sizeof(T) == 4) pd[k] += DL[k * N + i];
+                }
+            }
+            const T* V = reinterpret_cast<const T*>(b.v);
+            pv[0] = V[i]; pv[1] = V[N + i]; pv[2] = V[2 * N + i];
+            if (S.thermo) {
+                const T4 z = reinterpret_cast<const T4*>(b.xi)[i];
+                pz[0] = z.x; pz[1] = z.y; pz[2] = z.z;
+            }
+        }
+        T f[3] = {(T)0, (T)0, (T)0};
+        if (S.pot == POT_SW) {
+            int4* a4 = reinterpret_cast<int4*>(b.lacc) + i;
+            const int4 q = *a4;
+            *a4 = make_int4(0, 0, 0, 0);
+            const T inv = (T)(1.0 / (double)kLegScale);
+            f[0] = (T)q.x * inv; f[1] = (T)q.y * inv; f[2] = (T)q.z * inv;
+        }
+        finish_atom<T, MODE>(b, S, st, i, f, (T)0, false, pd, pv, pz, s_xm, red);
     }
     block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
@@ -1724,7 +1831,9 @@ __global__ void k_decode_ev(const long long* acc, double* out7) {
 // ------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------
-bool lanes_supported(int lanes) { return lanes == 1 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
+bool lanes_supported(int lanes) {
+    return lanes == 0 || lanes == 1 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32;
+}
 
 // With a worklist (engine) the per-tile rebuild kernels get a bounded grid and walk the
 // flagged tiles; without one (stateless calls) they cover every tile.
@@ -1828,9 +1937,13 @@ template <typename T>
 static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
     // an FP64 shell of 32 atoms per block does not fit the 48 KB static shared limit: 4 -> 8
     switch (lanes) {
+        case 0:   // one thread per atom, scatter form: FP32 only
+            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
+            else k_edges1<T, true><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
+            break;
         case 1:   // one thread per atom: FP32 only (the FP64 columns exceed the shared limit)
             if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
-            else k_edges1<T><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
+            else k_edges1<T, false><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
             break;
         case 4:
             if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
@@ -1854,6 +1967,7 @@ void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode,
 template <typename T, int MODE>
 static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
     switch (lanes) {
+        case 0: k_finish<T, MODE><<<ntiles, kTile, 0, s>>>(b); break;
         case 1: k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b); break;
         case 2: k_gather<T, MODE, 2><<<ntiles * 2, kTile, 0, s>>>(b); break;
         case 8: k_gather<T, MODE, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;

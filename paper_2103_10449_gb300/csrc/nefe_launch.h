@@ -55,6 +55,7 @@ struct Bufs {
     int* uf_cnt;             // [ntot] their lengths
     void* uf_F;              // [ntot] UF force and atom energy of the step (T4)
     const int* uf_tiles;     // tiles of the UF systems (per-step UF kernel), or NULL: every tile
+    int* lacc;               // [ntot][4] int32 force accumulators of the scatter form (2^-21 eV/A)
 };
 
 enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };

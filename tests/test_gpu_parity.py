@@ -206,7 +206,7 @@ def test_frenkel_ladd_trajectory_fp64_matches_oracle(N):
     assert res["T"] == pytest.approx(ro["T"], rel=1e-7)
 
 
-@pytest.mark.parametrize("lanes", [1, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [0, 1, 4, 8, 16, 32])
 def test_frenkel_ladd_trajectory_fp32_close_to_oracle(N, lanes):
     orc, res, x, v = _fl_pair(0, nsteps=100, lanes=lanes)
     ro = orc.results()
@@ -233,13 +233,16 @@ def test_list_lanes_leave_the_run_bitwise_unchanged(N, precision):
         assert r[1]["W"] == runs[0][1]["W"] and np.array_equal(r[2], runs[0][2])
 
 
-def test_run_is_bitwise_deterministic(N):
-    a = _fl_pair(0, nsteps=200)
-    b = _fl_pair(0, nsteps=200)
+@pytest.mark.parametrize("lanes", [None, 0])
+def test_run_is_bitwise_deterministic(N, lanes):
+    """Gather form (default lanes) and scatter form (integer accumulators): identical reruns."""
+    a = _fl_pair(0, nsteps=200, lanes=lanes)
+    b = _fl_pair(0, nsteps=200, lanes=lanes)
     assert a[1]["W"] == b[1]["W"] and np.array_equal(a[2], b[2])
 
 
-def test_thread_per_atom_pass_a_with_spilled_shells(N):
+@pytest.mark.parametrize("lanes", [1, 0])
+def test_thread_per_atom_pass_a_with_spilled_shells(N, lanes):
     """A random liquid has in-cutoff shells beyond the 8 entries the one-thread-per-atom pass A
     keeps in shared memory; the rest live in its global spill area.  Ten FP32 steps against the
     FP64 oracle (NVT, 1700 K)."""
@@ -251,7 +254,7 @@ def test_thread_per_atom_pass_a_with_spilled_shells(N):
     ctx = nefe.Context(precision=nefe.NEFE_FP32, skin=SKIN, nbr_cap=CAP)
     s = ctx.add_system(x0, box, v=v0)
     ctx.set_thermostat(s, 1700.0, 0.1, 83)
-    ctx.set_tuning(1)
+    ctx.set_tuning(lanes)
     ctx.run(10)
     _, mx = ctx.shell_stats()
     res = ctx.results(s)
