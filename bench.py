@@ -147,18 +147,103 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_context(N, replicas, precision, seed0=1000, stream=None, skin=None):
+def build_context(N, replicas, precision, seed0=1000, stream=None, skin=None, first=0):
+    """Replicas first .. first + replicas - 1 of the benchmark workload (replica u: seed seed0 + u,
+    forward when u is even, backward when odd), so a sharded job holds the same set of replicas
+    whatever the number of ranks."""
     from paper_2103_10449_gb300 import inputs as I
     x, box = I.diamond(NCELL, NCELL, NCELL)
     sv = math.sqrt(KB * T_SW / (MASS * MVV2E))
     ctx = N.Context(precision=precision, dt=0.001, skin=SKIN if skin is None else skin, nbr_cap=48, stream=stream)
-    for r in range(replicas):
-        v = I.gaussian_velocities(len(x), sv, seed0 + r)
+    for u in range(first, first + replicas):
+        v = I.gaussian_velocities(len(x), sv, seed0 + u)
         s = ctx.add_system(x, box, v=v, r0=x, mass=MASS)
-        ctx.set_thermostat(s, T_SW, 0.1, seed0 + r)
-        ctx.set_schedule(s, N.NEFE_SCHED_FL, direction=1 if r % 2 == 0 else -1, nsteps=NSCHED, k_E=K_E)
+        ctx.set_thermostat(s, T_SW, 0.1, seed0 + u)
+        ctx.set_schedule(s, N.NEFE_SCHED_FL, direction=1 if u % 2 == 0 else -1, nsteps=NSCHED, k_E=K_E)
     ctx.setup()
     return ctx, len(x)
+
+
+class FLEngine:
+    """One rank's replicas [lo, hi) of the Frenkel-Ladd benchmark workload, driven by
+    sharding.run_sharded: equilibrated, autotuned (or fixed lanes), profiled."""
+
+    def __init__(self, N, torch, lo, hi, args):
+        self.N, self.torch = N, torch
+        self.stream = torch.cuda.Stream()
+        self.lo, self.hi = lo, hi
+        self.ctx, self.natoms = build_context(N, hi - lo, N.NEFE_FP32, stream=self.stream, skin=args.skin, first=lo)
+        self.ctx.run(args.equil)
+        if args.tuning:
+            la, lb = (int(v) for v in args.tuning.split(","))
+            self.ctx.set_tuning(la, lb)
+        else:
+            self.ctx.autotune()
+        self.ctx.set_profiling(True)
+
+    def warmup(self, k):
+        for _ in range(k):
+            self.ctx.run(MD_STEPS)
+        self.ctx.sync()
+        self.launches0 = self.ctx.launch_count()
+
+    def timed(self, k):
+        return time_steps(self.torch, self.ctx, self.stream, k, MD_STEPS)
+
+    def rows(self):
+        return [(self.lo + j, r["W"], r["lambda"], int(r["error"])) for j, r in enumerate(self.ctx.results_all())]
+
+
+class DcciEngine:
+    """One rank's pairs [lo, hi) of the batched dCCI workload (64 Si-cd / beta-Sn pairs of
+    log-uniform size), driven by sharding.run_sharded."""
+
+    def __init__(self, N, torch, lo, hi, sizes):
+        from paper_2103_10449_gb300 import inputs as I
+        self.N, self.torch = N, torch
+        self.stream = torch.cuda.Stream()
+        sv = math.sqrt(KB * 400.0 / (MASS * MVV2E))
+        self.ctx = N.Context(precision=N.NEFE_FP32, dt=0.001, skin=SKIN, nbr_cap=48, stream=self.stream)
+        self.pairs = []
+        self.lo = lo
+        for k in range(lo, hi):
+            n = sizes[k]
+            xa, ba = I.diamond(*I.diamond_cells_for(n))
+            xb, bb = I.beta_tin(*I.beta_tin_cells_for(n))
+            a = self.ctx.add_system(xa, ba, v=I.gaussian_velocities(len(xa), sv, 3000 + 2 * k), mass=MASS)
+            b = self.ctx.add_system(xb, bb, v=I.gaussian_velocities(len(xb), sv, 3001 + 2 * k), mass=MASS)
+            for sidx, seed in ((a, 3000 + 2 * k), (b, 3001 + 2 * k)):
+                self.ctx.set_thermostat(sidx, 400.0, 0.1, seed)
+            self.ctx.set_barostat(a, N.NEFE_BARO_ISO, 10.0, 0.5)
+            self.ctx.set_barostat(b, N.NEFE_BARO_ANISO, 10.0, 0.5)
+            self.pairs.append(self.ctx.pair_dcci(a, b, 400.0, 10.0, N.NEFE_DCCI_PRESS, 10.0, 15.0, 100000))
+        self.ctx.setup()
+        self.ctx.run(320)
+        self.ctx.autotune()
+
+    def warmup(self, k):
+        self.ctx.run(k * MD_STEPS)
+        self.ctx.sync()
+
+    def timed(self, k):
+        return time_steps(self.torch, self.ctx, self.stream, k, MD_STEPS)
+
+    def rows(self):
+        out = []
+        for j, p in enumerate(self.pairs):
+            T, P, lam, err = self.ctx.pair(p)
+            out.append((self.lo + j, T, P, int(err)))
+        return out
+
+
+def dcci_pair_atoms(sizes):
+    from paper_2103_10449_gb300 import inputs as I
+    out = []
+    for n in sizes:
+        nx, ny, nz = I.diamond_cells_for(n)
+        mx, my, mz = I.beta_tin_cells_for(n)
+        out.append(8 * nx * ny * nz + 4 * mx * my * mz)
+    return out
 
 
 def free_energy_error(N, reps=8, n_eq=500, n_sw=2000):
@@ -253,20 +338,41 @@ def precision_errors(N, reps=4, n_eq=2000, n_dcci=10000, n_rs=5000):
             c.set_barostat(s, N.NEFE_BARO_ISO, P_rs, 1.0)
             c.set_schedule(s, N.NEFE_SCHED_RS, nsteps=n_rs, lambda_f=0.5, P_GPa=P_rs)
             rs.append(s)
+        # pressure switching of both solids from 13.09 to 14 GPa at 400 K (the step that fixes the
+        # 400 K coexistence pressure): the switching work per atom of each phase
+        asw = []
+        for r in range(reps):
+            for k, mode in ((0, N.NEFE_BARO_ISO), (1, N.NEFE_BARO_ANISO)):
+                x, v, b = st[2 * r + k]
+                s = c.add_system(x, b, v=v)
+                c.set_thermostat(s, T0, 0.1, 8400 + 2 * r + k)
+                c.set_barostat(s, mode, P0, 1.0)
+                c.set_schedule(s, N.NEFE_SCHED_AS, nsteps=n_rs, P0_GPa=P0, P1_GPa=14.0)
+                asw.append(s)
         c.run(n_rs)
         w = np.array([c.results(s)["W"] / len(xa) for s in rs])
+        w_as = np.array([c.results(s)["W"] / (len(xa) if j % 2 == 0 else len(xb)) for j, s in enumerate(asw)])
+        v_as = np.array([c.results(s)["V"] / (len(xa) if j % 2 == 0 else len(xb)) for j, s in enumerate(asw)])
         c.run(n_dcci - n_rs)
         pc = np.array([c.pair(p)[1] for p in pids])
         errs = sum(int(r["error"] != 0) for r in c.results_all())
         c.close()
-        out[name] = (pc, w, errs)
-    p64, w64, e64 = out["fp64"]
-    p32, w32, e32 = out["fp32"]
+        out[name] = (pc, w, errs, w_as, v_as)
+    p64, w64, e64, a64, v64 = out["fp64"]
+    p32, w32, e32, a32, _ = out["fp32"]
+    # the coexistence pressure moves by the error of G_cd - G_beta-tin over the volume difference
+    d_as = (a32[0::2] - a64[0::2]).mean() - (a32[1::2] - a64[1::2]).mean()
+    dv = v64[0::2].mean() - v64[1::2].mean()
     return {"dcci_P_coex": {"fp64_GPa": float(p64.mean()), "fp32_GPa": float(p32.mean()),
                             "err_GPa": float(p32.mean() - p64.mean()),
                             "stat_err_GPa": float(p64.std(ddof=1) / math.sqrt(reps)),
                             "protocol": f"{reps} Si-cd/beta-Sn pairs (8000 + 8000 atoms), temperature control "
                                         f"400 -> 600 K over {n_dcci} steps from 13.09 GPa"},
+            "as_W": {"cd_err_meV_per_atom": float(1000.0 * (a32[0::2] - a64[0::2]).mean()),
+                     "betasn_err_meV_per_atom": float(1000.0 * (a32[1::2] - a64[1::2]).mean()),
+                     "implied_P_coex_err_GPa": float(d_as / dv * 160.21766340),
+                     "protocol": f"{reps} Si-cd and {reps} beta-Sn replicas, pressure switching 13.09 -> 14 GPa at "
+                                 f"400 K over {n_rs} steps; P_coex error = error of (G_cd - G_beta-Sn) / dV"},
             "rs_W": {"fp64_eV_per_atom": float(w64.mean()), "fp32_eV_per_atom": float(w32.mean()),
                      "err_meV_per_atom": float(1000.0 * (w32.mean() - w64.mean())),
                      "stat_err_meV_per_atom": float(1000.0 * w64.std(ddof=1) / math.sqrt(reps)),
@@ -295,10 +401,12 @@ def differentiation_throughput(N, torch):
         eg = torch.empty(8, dtype=torch.float64, device="cuda")
         N.nefe_neighbor_build(xd, n, box, rcs, cap, nbr, cnt)
         row = {}
+        grads = {}
         for name, prec in (("fp32", N.NEFE_FP32), ("fp64", N.NEFE_FP64)):
             for _ in range(2):
                 N.nefe_sw_energy_grad(xd, n, box, rcs, nbr, cnt, cap, prm, prec, f, eg)
             torch.cuda.synchronize()
+            grads[name] = eg.cpu().numpy().copy()
             reps = 5
             t0 = time.perf_counter()
             for _ in range(reps):
@@ -306,6 +414,9 @@ def differentiation_throughput(N, torch):
             torch.cuda.synchronize()
             row[name] = n * reps / (time.perf_counter() - t0)
         out["grad_sweep_atoms_per_s"][str(n)] = row
+        g32, g64 = grads["fp32"], grads["fp64"]
+        out.setdefault("dE_dtheta_fp32_rel_err", {})[str(n)] = float(
+            np.max(np.abs(g32[1:] - g64[1:])) / np.max(np.abs(g64[1:])))
         del xd, nbr, cnt, f
     x, box = I.liquid(32768, 0.05425, seed=51)
     v = I.gaussian_velocities(len(x), math.sqrt(KB * 1700.0 / (MASS * MVV2E)), 52)
@@ -331,41 +442,28 @@ def differentiation_throughput(N, torch):
     return out
 
 
-def dcci_batched_throughput(N, torch, pairs=64, steps=5):
+def dcci_batched_throughput(N, torch, pairs=64, steps=5, rank=0, world=1, dist=None, barrier=None):
     """The batched dCCI workload: `pairs` coupled Si-cd / beta-Sn pairs of uneven sizes
-    (log-uniform 512..32768 atoms per phase, from a fixed seed) in one context, pressure-
-    controlled coexistence integration from 10 GPa at 400 K (Eq. l_coex_discreted), FP32
-    kernels, captured graph; atom-steps/s over `steps` graph replays after equilibration and
-    autotuning."""
+    (log-uniform 512..32768 atoms per phase, from a fixed seed), pressure-controlled coexistence
+    integration from 10 GPa at 400 K (Eq. l_coex_discreted), FP32 kernels, captured graph;
+    atom-steps/s over `steps` graph replays after equilibration and autotuning.  With several
+    ranks each takes a contiguous range of pairs balanced by atom count (a pair never splits:
+    its two phases exchange U and V every step) and the coexistence estimates of all pairs are
+    gathered at the end."""
     from paper_2103_10449_gb300 import inputs as I
+    from paper_2103_10449_gb300 import sharding as SH
     sizes = I.log_uniform_sizes(pairs, 512, 32768, seed=2021)
-    sv = math.sqrt(KB * 400.0 / (MASS * MVV2E))
-    stream = torch.cuda.Stream()
-    ctx = N.Context(precision=N.NEFE_FP32, dt=0.001, skin=SKIN, nbr_cap=48, stream=stream)
-    natoms = 0
-    for k, n in enumerate(sizes):
-        xa, ba = I.diamond(*I.diamond_cells_for(n))
-        xb, bb = I.beta_tin(*I.beta_tin_cells_for(n))
-        a = ctx.add_system(xa, ba, v=I.gaussian_velocities(len(xa), sv, 3000 + 2 * k), mass=MASS)
-        b = ctx.add_system(xb, bb, v=I.gaussian_velocities(len(xb), sv, 3001 + 2 * k), mass=MASS)
-        for sidx, seed in ((a, 3000 + 2 * k), (b, 3001 + 2 * k)):
-            ctx.set_thermostat(sidx, 400.0, 0.1, seed)
-        ctx.set_barostat(a, N.NEFE_BARO_ISO, 10.0, 0.5)
-        ctx.set_barostat(b, N.NEFE_BARO_ANISO, 10.0, 0.5)
-        ctx.pair_dcci(a, b, 400.0, 10.0, N.NEFE_DCCI_PRESS, 10.0, 15.0, 100000)
-        natoms += len(xa) + len(xb)
-    ctx.setup()
-    ctx.run(320)
-    ctx.autotune()
-    ctx.run(2 * MD_STEPS)
-    ctx.sync()
-    wall = time_steps(torch, ctx, stream, steps, MD_STEPS)
-    errors = sum(1 for r in ctx.results_all() if r["error"] != 0)
-    ctx.close()
+    atoms = dcci_pair_atoms(sizes)
+    out = SH.run_sharded(atoms, rank, world, lambda lo, hi: DcciEngine(N, torch, lo, hi, sizes), 2, steps,
+                         MD_STEPS, dist=dist, device=torch.device("cuda", torch.cuda.current_device()),
+                         barrier=barrier)
+    errors = sum(1 for r in out["rows"] if r[3] != 0)
+    out["engine"].ctx.close()
     return {"workload": f"{pairs} Si-cd/beta-Sn dCCI pairs, 512..32768 atoms per phase (log-uniform), "
                         f"pressure control 10 -> 15 GPa at 400 K, FP32 kernels",
-            "atoms": natoms, "atom_steps_per_s": natoms * MD_STEPS * steps / wall,
-            "systems_with_errors": errors}
+            "atoms": int(sum(atoms)), "atom_steps_per_s": out["value"], "ranks": world,
+            "pairs_per_rank": [list(r) for r in SH.shard_units(atoms, world)],
+            "pairs_gathered": len(out["rows"]), "pairs_with_errors": errors}
 
 
 def rs_npt_batched_throughput(N, torch, per_phase=20, steps=5):
@@ -461,9 +559,23 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.replicas),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_cores_available": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def spawn_ranks(args):
+    """`--gpus N` without a launcher: start N ranks (one process per GPU) through torch's launcher,
+    exactly as a torchrun launch would; rank 0 prints the JSON line."""
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
 
 
 def main():
@@ -472,7 +584,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nefe", choices=["nefe", "reference"])
-    ap.add_argument("--replicas", type=int, default=128)
+    ap.add_argument("--replicas", type=int, default=128, help="replicas per GPU")
     ap.add_argument("--equil", type=int, default=3000,
                     help="untimed MD steps before warm-up (thermalises the crystals)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
@@ -483,6 +595,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1 and args.impl == "nefe":
+        sys.exit(spawn_ranks(args))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -491,59 +605,60 @@ def main():
 
     import torch
     dist = None
+    torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(local)
 
     from paper_2103_10449_gb300 import nefe as N
+    from paper_2103_10449_gb300 import sharding as SH
     N.load()
     R = args.replicas
-    stream = torch.cuda.Stream()
-    from paper_2103_10449_gb300 import sharding as SH
-    ctx, natoms = build_context(N, R, N.NEFE_FP32, seed0=SH.rank_seed(1000, rank), stream=stream, skin=args.skin)
-    ctx.run(args.equil)
-    if args.tuning:
-        la, lb = (int(v) for v in args.tuning.split(","))
-        ctx.set_tuning(la, lb)
-    else:
-        ctx.autotune()
-    ctx.set_profiling(True)
-    for _ in range(args.warmup):
-        ctx.run(MD_STEPS)
-    ctx.sync()
+    dev = torch.device("cuda", local)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the whole job: world x R replicas, each rank takes its contiguous share (weak scaling)
     clocks = ClockSampler(local)
-    launches0 = ctx.launch_count()
-    barrier()
-    clocks.start()
-    time.sleep(0.3)
-    wall = time_steps(torch, ctx, stream, args.steps, MD_STEPS)
-    barrier()
+
+    def clocks_start():
+        clocks.start()
+        time.sleep(0.3)
+
+    run = SH.run_sharded([8 * NCELL ** 3] * (world * R), rank, world, lambda lo, hi: FLEngine(N, torch, lo, hi, args),
+                         args.warmup, args.steps, MD_STEPS, dist=dist, device=dev, barrier=barrier,
+                         before_timed=clocks_start, after_timed=None)
     clk = clocks.stop()
-    launches = ctx.launch_count() - launches0
+    eng = run["engine"]
+    ctx = eng.ctx
+    natoms = eng.natoms
+    wall = run["wall_max"]
+    value = run["value"]
+    launches = ctx.launch_count() - eng.launches0
     a_us, b_us, nsamp = ctx.profile()
     mean_cnt, max_cnt, nbuild = ctx.list_stats(-1)
-    errors = sum(1 for r in ctx.results_all() if r["error"] != 0)
-    wall = SH.max_over_ranks(wall, dist, device=torch.device("cuda", local))
-    atoms = natoms * R
-    value = SH.aggregate_throughput([atoms * MD_STEPS * args.steps] * world, wall)
+    errors = sum(1 for r in run["rows"] if r[3] != 0)
+    atoms = natoms * (run["range"][1] - run["range"][0])
 
     # roofline of the dominant kernel (the longer force pass), from live CUDA-event durations
     m_shell, _ = ctx.shell_stats()
+    lanes = list(ctx.lanes())
     bytes_a = PASS_A_FIXED + 4.0 * mean_cnt + 20.0 * m_shell
     bytes_b = PASS_B_FIXED + 20.0 * m_shell
+    if lanes[0] == 0:
+        # scatter form: pass A reads own mirror, row length and row, and adds the leg forces into
+        # 16-byte accumulators (L2-resident reductions, not counted); pass B streams the
+        # epilogue operands (accumulator 16, spring offset 16, displacement 24, noise 16, v 12 +
+        # 12, force 16)
+        bytes_a = 16 + 4 + 4.0 * mean_cnt + 4
+        bytes_b = 16 + 16 + 24 + 16 + 12 + 12 + 16
     if b_us > a_us:
-        kkey, kname, kbytes, kus = "k_gather", "k_gather (force pass B: leg forces of the neighbours' triplets, springs, Langevin, kick)", bytes_b, b_us
+        kkey, kname, kbytes, kus = "k_gather", "force pass B (gather or scatter-form epilogue: springs, Langevin, kick)", bytes_b, b_us
     else:
-        kkey, kname, kbytes, kus = "k_edges", "k_edges (force pass A: shell, pair terms, leg forces of the triplets centred on the atom)", bytes_a, a_us
+        kkey, kname, kbytes, kus = "k_edges", "force pass A (shell, pair terms, triplet leg forces)", bytes_a, a_us
     achieved = kbytes * atoms / (kus * 1e-6) / 1e9
     peak, peak_kind = peaks()
     tr = recorded_traffic(kkey)
@@ -554,18 +669,24 @@ def main():
                 "pass_a_us_mean": a_us, "pass_b_us_mean": b_us,
                 "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak,
                 "step_bytes_per_atom_step": STEP_BYTES,
-                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "lanes_per_atom": ctx.lanes()[0],
-                "lanes_pass_a_pass_b_list": list(ctx.lanes())}
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "lanes_per_atom": lanes[0],
+                "lanes_pass_a_pass_b_list": lanes}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": workload_config(R, args.skin), "roofline": roofline, "clocks": clk, "gpu_launches": launches,
             "list": {"mean_row": mean_cnt, "max_row": max_cnt, "builds": nbuild, "mean_shell": m_shell},
-            "systems_with_errors": errors}
-    del ctx
+            "systems_with_errors": errors,
+            "sharding": {"ranks": world, "replicas_per_rank": R, "replicas_gathered": len(run["rows"]),
+                         "collectives": "max of the timed interval, all-gather of per-replica results (after the timed region)"}}
+    ctx.close()
+    del eng
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and world > 1:
+        # several ranks: the batched dCCI workload sharded over all ranks (pairs by atom count)
+        line["dcci_batched"] = dcci_batched_throughput(N, torch, rank=rank, world=world, dist=dist, barrier=barrier)
+    if not args.no_extras and world == 1:
         # e2e through the public API with host buffers: upload state, run, read results
         ctx, _ = build_context(N, R, N.NEFE_FP32, seed0=1000)
         ntot = natoms * R
@@ -611,6 +732,7 @@ def main():
         line["rs_npt_batched"] = rs_npt_batched_throughput(N, torch)
         cps, nst, dt = cpu_baseline_sample()
         line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "host_cores_available": os.cpu_count(),
                                 "sample": f"{nst} FP64-oracle MD steps of one 8000-atom replica ({dt:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)

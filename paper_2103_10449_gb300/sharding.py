@@ -68,3 +68,35 @@ def gather_results(rows: list, dist=None) -> list:
     for part in out:
         merged.extend(part)
     return merged
+
+
+def run_sharded(atoms_per_unit: Sequence[int], rank: int, world: int, build, warmup: int, steps: int,
+                md_steps_per_step: int, dist=None, device=None, barrier=None, before_timed=None,
+                after_timed=None) -> dict:
+    """One rank's part of a replica job, the orchestration the benchmark runs on every rank.
+
+    The units (independent replicas or dCCI pairs, ``atoms_per_unit`` atoms each) are split by
+    ``shard_units``; ``build(lo, hi)`` returns this rank's engine for units [lo, hi), an object
+    with ``warmup(k)``, ``timed(k)`` (seconds of k timed steps, measured on the device) and
+    ``rows()`` (one result row per unit).  The timed region is bracketed by ``barrier`` (and
+    ``before_timed`` / ``after_timed``, e.g. a clock sampler); afterwards the slowest rank's time,
+    the whole-job throughput (atom-steps of all ranks over that time) and every unit's result
+    row (all-gathered, in unit order) are returned.  No collective runs inside the timed region."""
+    lo, hi = shard_units(atoms_per_unit, world)[rank]
+    eng = build(lo, hi)
+    eng.warmup(warmup)
+    if barrier is not None:
+        barrier()
+    if before_timed is not None:
+        before_timed()
+    wall = eng.timed(steps)
+    if barrier is not None:
+        barrier()
+    if after_timed is not None:
+        after_timed()
+    wall_max = max_over_ranks(wall, dist, device)
+    mine = float(sum(atoms_per_unit[lo:hi])) * md_steps_per_step * steps
+    done = gather_results([mine], dist)
+    return {"value": aggregate_throughput(done, wall_max), "wall": wall, "wall_max": wall_max,
+            "range": (lo, hi), "atom_steps_per_rank": done, "rows": gather_results(eng.rows(), dist),
+            "engine": eng}

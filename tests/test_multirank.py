@@ -67,3 +67,62 @@ def test_two_rank_gloo_timing_and_gather():
     assert value == pytest.approx(sum(sizes) * 32 * 10 / 2.0)
     assert [u for u, _ in rows] == list(range(len(sizes)))
     assert seed1 == 1000 + 7919
+
+
+class _StubEngine:
+    """Host stand-in for a rank's engine (no device): 'timed' reports a fixed duration that
+    differs by rank, 'rows' one result per unit."""
+
+    def __init__(self, lo, hi, rank):
+        self.lo, self.hi, self.rank = lo, hi, rank
+        self.warm = 0
+
+    def warmup(self, k):
+        self.warm = k
+
+    def timed(self, k):
+        return 0.5 * k * (1 + self.rank)
+
+    def rows(self):
+        return [(u, 2.0 * u, self.rank) for u in range(self.lo, self.hi)]
+
+
+def _orchestration_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sizes = [int(s) for s in I.log_uniform_sizes(64, 512, 32768, seed=2021)]
+    calls = []
+    res = S.run_sharded(sizes, rank, world, lambda lo, hi: _StubEngine(lo, hi, rank), 3, 4, 32, dist=dist,
+                        barrier=dist.barrier, before_timed=lambda: calls.append("before"),
+                        after_timed=lambda: calls.append("after"))
+    if rank == 0:
+        out.put((res["value"], res["wall_max"], res["rows"], res["range"], res["atom_steps_per_rank"], calls,
+                 res["engine"].warm))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_gloo_runs_the_benchmark_orchestration():
+    """sharding.run_sharded, the function bench.py runs on every rank (for the replica benchmark
+    and the batched dCCI pairs), with a host stub engine: the units are split by atom count, the
+    slowest rank's time is the job's time, the throughput counts every rank's atom-steps, and every
+    unit's result row comes back in unit order."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_orchestration_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    value, wall_max, rows, rng, per_rank, calls, warm = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    sizes = [int(s) for s in I.log_uniform_sizes(64, 512, 32768, seed=2021)]
+    parts = S.shard_units(sizes, 2)
+    assert rng == parts[0] and warm == 3 and calls == ["before", "after"]
+    assert wall_max == 0.5 * 4 * 2                       # rank 1 is the slower one
+    assert per_rank == [float(sum(sizes[a:b])) * 32 * 4 for a, b in parts]
+    assert value == pytest.approx(sum(sizes) * 32 * 4 / wall_max)
+    assert [r[0] for r in rows] == list(range(len(sizes)))
+    assert [r[2] for r in rows] == [0] * (parts[0][1] - parts[0][0]) + [1] * (parts[1][1] - parts[1][0])
