@@ -157,6 +157,18 @@ __device__ __forceinline__ void block_sum_to_acc(T (&v)[K], long long* acc_sys, 
     }
 }
 
+// Sum of the kSlots fixed-point slots of one per-system value.  The loads are independent, so
+// they are issued together (one memory latency, not kSlots of them).
+__device__ __forceinline__ long long slot_sum(const long long* slots) {
+    long long v[kSlots];
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) v[sl] = slots[sl];
+    long long sum = 0;
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) sum += v[sl];
+    return sum;
+}
+
 // Per-block table of the 27 cell-offset vectors o h (o in {-1,0,1}^3), indexed by the list
 // entry's code.  Every thread of the block must call it.
 template <typename T>
@@ -209,6 +221,34 @@ __device__ __forceinline__ TileAtom tile_of(const Bufs& b, int tile) {
     const DevSys& S = b.sys[t.sys];
     t.first = S.off + (tile - S.tile0) * kTile;
     t.count = min(kTile, S.off + S.n - t.first);
+    return t;
+}
+
+// A tile's system descriptor and state copied into shared memory by all threads of the block
+// (independent 4-byte loads: one memory latency, instead of one per cache line of the structs
+// that the kernel's field accesses would otherwise wait for, one after the other), and the tile.
+// Writes to the state (flags, error bits) still go to the global copy.  Every thread of the block
+// must call it; it ends with a barrier.
+struct StagedSys {
+    DevSys S;
+    DevState st;
+};
+__device__ __forceinline__ TileAtom stage_tile(const Bufs& b, int tile, StagedSys& sh) {
+    const int sys = b.tile_sys[tile];
+    const uint32_t* gs = reinterpret_cast<const uint32_t*>(b.sys + sys);
+    const uint32_t* gt = reinterpret_cast<const uint32_t*>(b.st + sys);
+    uint32_t* ds = reinterpret_cast<uint32_t*>(&sh.S);
+    uint32_t* dt = reinterpret_cast<uint32_t*>(&sh.st);
+    constexpr int ws = (int)(sizeof(DevSys) / 4), wt = (int)(sizeof(DevState) / 4);
+    for (int w = threadIdx.x; w < ws + wt; w += blockDim.x) {
+        if (w < ws) ds[w] = gs[w];
+        else dt[w - ws] = gt[w - ws];
+    }
+    __syncthreads();
+    TileAtom t;
+    t.sys = sys;
+    t.first = sh.S.off + (tile - sh.S.tile0) * kTile;
+    t.count = min(kTile, sh.S.off + sh.S.n - t.first);
     return t;
 }
 
@@ -454,6 +494,7 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
+    DevState& gst = st;
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
@@ -528,7 +569,7 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
                 if (p0 + u >= hi) break;
                 const int j = unpack_index(xj[u].w);
                 if (j < S.off || j >= S.off + S.n) {
-                    atomicOr(&st.err, NEFE_ERR_CELL);
+                    atomicOr(&gst.err, NEFE_ERR_CELL);
                     continue;
                 }
                 if (j == i && o == 13) continue;
@@ -569,7 +610,7 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
     }
     if (lane == 0) {
         b.cnt[i] = count;
-        if (count > cap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
+        if (count > cap) atomicOr(&gst.err, NEFE_ERR_NBR_OVERFLOW);
     }
     __syncwarp(gmask);                           // shared tables reused by the next item
 }
@@ -581,8 +622,7 @@ __global__ void __launch_bounds__(kTile) k_nlist(Bufs b) {
     __shared__ int cnt_s[G];
     if (b.rtiles) {
         const int n = *b.rcount * L;
-        for (int w = blockIdx.x; w < n; w += gridDim.x)
-            nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cnt_s);
+        for (int w = blockIdx.x; w < n; w += gridDim.x) nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cnt_s);
     } else {
         nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, buf, cnt_s);
     }
@@ -810,6 +850,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
     const TileAtom ta = tile_of(b, blockIdx.x);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
+    DevState& gst = st;
     T xs_sum[3] = {(T)0, (T)0, (T)0};
     if ((int)threadIdx.x < ta.count) {
         const int i = ta.first + threadIdx.x;
@@ -856,7 +897,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
             const T dd = hmoved ? m[k] - xav[k] * pick<T>(st.h[k] / st.hb[k], st.rho_f[k]) : dh[k] + dl[k];
             dd2 += dd * dd;
         }
-        if (dd2 > pick<T>(st.thr2, st.thr2_f) && !st.rebuild) atomicOr(&st.rebuild, 1);
+        if (dd2 > pick<T>(st.thr2, st.thr2_f) && !st.rebuild) atomicOr(&gst.rebuild, 1);
         if (S.thermo) {
             T z[3];
             Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)st.k, (uint64_t)(i - S.off), z);
@@ -864,7 +905,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
             xs_sum[0] = z[0]; xs_sum[1] = z[1]; xs_sum[2] = z[2];
         }
     }
-    block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &st.err);
+    block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &gst.err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1132,16 +1173,18 @@ __device__ __forceinline__ void red_force(int* acc4, float x, float y, float z, 
     atomicAdd(acc4 + 2, __float2int_rn(z * kLegScale));
 }
 
+constexpr int kEdges1K1 = kShell1Shared;
+
+// One work item of the thread-per-atom pass A: half a tile (64 atoms).  Every thread of the
+// block calls it with the same item.
 template <typename T, bool SCATTER>
-__global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
+__device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4<T>::t (*sh_u)[kEdges1Threads],
+                                            T (*sh_r)[kEdges1Threads], typename V4<T>::t* soff) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
     // 20 bytes per shell entry and thread (occupancy is bound by this table):
     constexpr int K1 = kShell1Shared, KS = kShell1 - kShell1Shared;
-    __shared__ T4 sh_u[K1][NT];          // (d, r^2) after compaction, then (u, g)
-    __shared__ T sh_r[K1][NT];           // r
-    __shared__ T4 soff[27];
-    const int tile = blockIdx.x / (kTile / NT) + b.tile_base, part = blockIdx.x % (kTile / NT);
+    const int tile = item / (kTile / NT) + b.tile_base, part = item % (kTile / NT);
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
@@ -1205,6 +1248,10 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     if (m < kShell) Sj[m] = -1;
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    // Moments of the shell: G = sum_b g_b, m1 = sum_b g_b u_b, M = sum_b g_b u_b u_b^T.  Every
+    // sum over the partner edge b of a triplet (i; a, b) that the leg force needs is linear in
+    // these, so the triplets of an atom cost O(m) instead of O(m^2) (see phase 3).
+    T G = 0, m1x = 0, m1y = 0, m1z = 0, Mxx = 0, Myy = 0, Mzz = 0, Mxy = 0, Mxz = 0, Myz = 0;
     // 2. edges
     for (int a = 0; a < m; ++a) {
         const T4 d = get_u(a);
@@ -1218,10 +1265,21 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
         const T hc = (T)-0.5 * c;
         w0 += hc * d.x * d.x; w1 += hc * d.y * d.y; w2 += hc * d.z * d.z;
         w3 += hc * d.x * d.y; w4 += hc * d.x * d.z; w5 += hc * d.y * d.z;
-        put_u(a, mk4(d.x * ir, d.y * ir, d.z * ir, g));
+        const T ux = d.x * ir, uy = d.y * ir, uz = d.z * ir;
+        put_u(a, mk4(ux, uy, uz, g));
         put_r(a, r);
+        const T gx = g * ux, gy = g * uy, gz = g * uz;
+        G += g; m1x += gx; m1y += gy; m1z += gz;
+        Mxx += gx * ux; Myy += gy * uy; Mzz += gz * uz; Mxy += gx * uy; Mxz += gx * uz; Myz += gy * uz;
     }
-    // 3. leg forces
+    // 3. leg forces.  For edge a with c_b = u_a.u_b, over every partner b != a:
+    //   S1 = sum g_b (c_b - c0) u_b = M u_a - c0 m1 - g_a (1 - c0) u_a,
+    //   S2 = sum g_b (c_b - c0) c_b = u_a.M u_a - c0 u_a.m1 - g_a (1 - c0),
+    //   S3 = sum g_b (c_b - c0)^2   = u_a.M u_a - 2 c0 u_a.m1 + c0^2 G - g_a (1 - c0)^2
+    // (the sums over all b, minus the b = a term with c = 1).  The force the triplets (i; a, b)
+    // exert on leg atom j_a is L_a = (k1 S2 - k2 S3) u_a - k1 S1 with k1 = 2 eps lambda g_a / r_a,
+    // k2 = eps lambda dg_a/dr, and the atom's share of their energy is eps lambda g_a S3 / 2.
+    const T c0 = P.c0, c02 = c0 * c0;
     for (int a = 0; a < m; ++a) {
         const T4 ua = get_u(a);
         const T ga = ua.w, ra = get_r(a);
@@ -1231,19 +1289,19 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
         const T dga = -ga * P.gam * ida * ida * P.inv_sig;
         const T k1 = (T)2 * P.epslam * ga * xrcp(ra);
         const T k2 = P.epslam * dga;
-        T ax = 0, ay = 0, az = 0, cc = 0, eh = 0;
-        for (int bb = 0; bb < m; ++bb) {
-            if (bb == a) continue;
-            const T4 ub = get_u(bb);
-            const T gb = ub.w;
-            const T c = ua.x * ub.x + ua.y * ub.y + ua.z * ub.z;
-            const T dc = c - P.c0;
-            const T s1 = dc * gb;
-            const T t1 = k1 * s1;
-            ax += t1 * ub.x; ay += t1 * ub.y; az += t1 * ub.z;
-            cc += t1 * c - k2 * dc * s1;
-            eh += dc * s1;
-        }
+        const T Mux = Mxx * ua.x + Mxy * ua.y + Mxz * ua.z;
+        const T Muy = Mxy * ua.x + Myy * ua.y + Myz * ua.z;
+        const T Muz = Mxz * ua.x + Myz * ua.y + Mzz * ua.z;
+        const T q = ua.x * Mux + ua.y * Muy + ua.z * Muz;
+        const T pm = ua.x * m1x + ua.y * m1y + ua.z * m1z;
+        const T self = ga * ((T)1 - c0);
+        const T S2 = q - c0 * pm - self;
+        const T S3 = q - (T)2 * c0 * pm + c02 * G - self * ((T)1 - c0);
+        const T eh = S3;
+        const T cc = k1 * S2 - k2 * S3;
+        const T ax = k1 * (Mux - c0 * m1x - self * ua.x);
+        const T ay = k1 * (Muy - c0 * m1y - self * ua.y);
+        const T az = k1 * (Muz - c0 * m1z - self * ua.z);
         const T lx = cc * ua.x - ax, ly = cc * ua.y - ay, lz = cc * ua.z - az;
         if constexpr (SCATTER) red_force(b.lacc + 4 * (size_t)Sj[a], lx, ly, lz, &st.err);
         else Fl[a] = mk4(lx, ly, lz, (T)0);
@@ -1271,6 +1329,15 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     if constexpr (SCATTER) block_sum_to_acc<T, 8>(red8, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
 
+template <typename T, bool SCATTER>
+__global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
+    using T4 = typename V4<T>::t;
+    __shared__ T4 sh_u[kEdges1K1][kEdges1Threads];   // (d, r^2) after compaction, then (u, g)
+    __shared__ T sh_r[kEdges1K1][kEdges1Threads];    // r
+    __shared__ T4 soff[27];
+    edges1_item<T, SCATTER>(b, blockIdx.x, sh_u, sh_r, soff);
+}
+
 // Force pass B, L lanes per atom:
 //   F_SW(i) = P(i) + sum_{j in shell(i)} L_j(i),
 // L_j(i) being the leg force that the triplets centred on neighbour j exert on i, stored by
@@ -1284,17 +1351,27 @@ __device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, cons
                                             const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14]);
 template <typename T>
 __device__ __forceinline__ void noise_mean(const Bufs& b, const DevSys& S, int sys, T* s_xm);
+template <typename T>
+__device__ __forceinline__ void noise_mean_staged(const DevSys& S, const long long (*xi)[kSlots], T* s_xm);
 
 template <typename T, int MODE, int L>
 __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
     using T4 = typename V4<T>::t;
     constexpr int G = kTile / L;
     const int tile = blockIdx.x / L + b.tile_base, part = blockIdx.x % L;
-    const TileAtom ta = tile_of(b, tile);
-    const DevSys& S = b.sys[ta.sys];
-    DevState& st = b.st[ta.sys];
+    __shared__ __align__(16) StagedSys sh;
+    __shared__ long long s_xi[3][kSlots];
     __shared__ T s_xm[3];
-    if (MODE != FM_FORCES) noise_mean<T>(b, S, ta.sys, s_xm);
+    if (MODE != FM_FORCES) {   // the noise sums' slots, loaded with the descriptors
+        const int sys = b.tile_sys[tile];
+        const long long* xa = b.acc + (size_t)sys * ACC_N * kSlots + (size_t)ACC_XI * kSlots;
+        for (int w = threadIdx.x; w < 3 * kSlots; w += blockDim.x) s_xi[w / kSlots][w % kSlots] = xa[w];
+    }
+    const TileAtom ta = stage_tile(b, tile, sh);
+    const DevSys& S = sh.S;
+    const DevState& st = sh.st;
+    DevState& gst = b.st[ta.sys];
+    if (MODE != FM_FORCES) noise_mean_staged<T>(S, s_xi, s_xm);
     __syncthreads();
     const int lane = threadIdx.x % L, grp = threadIdx.x / L;
     const int lbase = ((threadIdx.x & 31) / L) * L;
@@ -1402,7 +1479,7 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
         }
         if (lane == 0) finish_atom<T, MODE>(b, S, st, i, f, e_i, true, pd, pv, pz, s_xm, red);
     }
-    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &gst.err);
 }
 
 // The epilogue of force pass B for atom i with SW (or zero) force f: the stateless output, or
@@ -1467,12 +1544,27 @@ __device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, cons
 
 // Per-system mean of this step's thermostat noise (the "zero yes" removal), from the
 // fixed-point sums of k_kick_drift, into s_xm[3].  Threads 0..2 write; the caller syncs.
+// The same mean from the noise sums' slots already copied to shared memory (3 x kSlots).
+template <typename T>
+__device__ __forceinline__ void noise_mean_staged(const DevSys& S, const long long (*xi)[kSlots], T* s_xm) {
+    if (threadIdx.x < 3) {
+        long long sum = 0;
+        for (int sl = 0; sl < kSlots; ++sl) sum += xi[threadIdx.x][sl];
+        if constexpr (sizeof(T) == 4) {
+            const float hi = (float)(int)(sum >> 32);
+            const float lo = (float)(unsigned)(sum & 0xffffffffLL) * 0x1p-32f;
+            s_xm[threadIdx.x] = (hi + lo) * S.inv_n_f;
+        } else {
+            s_xm[threadIdx.x] = (T)((double)sum / kFix / (double)S.n);
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void noise_mean(const Bufs& b, const DevSys& S, int sys, T* s_xm) {
     if (threadIdx.x < 3) {
         const long long* acc = b.acc + (size_t)sys * ACC_N * kSlots + (size_t)(ACC_XI + threadIdx.x) * kSlots;
-        long long sum = 0;
-        for (int sl = 0; sl < kSlots; ++sl) sum += acc[sl];
+        const long long sum = slot_sum(acc);
         if constexpr (sizeof(T) == 4) {   // sum 2^-32 / n from its 32-bit halves, FP32 only
             const float hi = (float)(int)(sum >> 32);
             const float lo = (float)(unsigned)(sum & 0xffffffffLL) * 0x1p-32f;
@@ -1490,11 +1582,19 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
     using T4 = typename V4<T>::t;
     const int tile = blockIdx.x + b.tile_base;
-    const TileAtom ta = tile_of(b, tile);
-    const DevSys& S = b.sys[ta.sys];
-    DevState& st = b.st[ta.sys];
+    __shared__ __align__(16) StagedSys sh;
+    __shared__ long long s_xi[3][kSlots];
     __shared__ T s_xm[3];
-    if (MODE != FM_FORCES) noise_mean<T>(b, S, ta.sys, s_xm);
+    if (MODE != FM_FORCES) {   // the noise sums' slots, loaded with the descriptors
+        const int sys = b.tile_sys[tile];
+        const long long* xa = b.acc + (size_t)sys * ACC_N * kSlots + (size_t)ACC_XI * kSlots;
+        for (int w = threadIdx.x; w < 3 * kSlots; w += blockDim.x) s_xi[w / kSlots][w % kSlots] = xa[w];
+    }
+    const TileAtom ta = stage_tile(b, tile, sh);
+    const DevSys& S = sh.S;
+    const DevState& st = sh.st;
+    DevState& gst = b.st[ta.sys];
+    if (MODE != FM_FORCES) noise_mean_staged<T>(S, s_xi, s_xm);
     __syncthreads();
     T red[14];
 #pragma unroll
@@ -1502,36 +1602,38 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
     if ((int)threadIdx.x < ta.count) {
         const int i = ta.first + threadIdx.x;
         const size_t N = b.ntot;
-        T pd[3] = {(T)0, (T)0, (T)0}, pv[3] = {(T)0, (T)0, (T)0}, pz[3] = {(T)0, (T)0, (T)0};
-        if (MODE != FM_FORCES) {
-            if (S.springs) {
-                const T4 d0 = reinterpret_cast<const T4*>(b.sd0)[i];
-                const T* DH = reinterpret_cast<const T*>(b.dhi);
-                const T* DL = reinterpret_cast<const T*>(b.dlo);
-                pd[0] = d0.x; pd[1] = d0.y; pd[2] = d0.z;
-                for (int k = 0; k < 3; ++k) {
-                    pd[k] += DH[k * N + i];
-                    if constexpr (sizeof(T) == 4) pd[k] += DL[k * N + i];
-                }
+        // every operand is loaded before the first is used, so the loads are in flight together
+        // (this kernel streams its operands; nothing else hides their latency)
+        const bool sw = S.pot == POT_SW, springs = MODE != FM_FORCES && S.springs;
+        const bool thermo = MODE != FM_FORCES && S.thermo;
+        int4* a4 = reinterpret_cast<int4*>(b.lacc) + i;
+        int4 q = make_int4(0, 0, 0, 0);
+        T4 d0 = mk4((T)0, (T)0, (T)0, (T)0), z = d0;
+        T dh[3] = {(T)0, (T)0, (T)0}, dl[3] = {(T)0, (T)0, (T)0}, pv[3] = {(T)0, (T)0, (T)0};
+        if (sw) q = *a4;
+        if (springs) {
+            const T* DH = reinterpret_cast<const T*>(b.dhi);
+            const T* DL = reinterpret_cast<const T*>(b.dlo);
+            d0 = reinterpret_cast<const T4*>(b.sd0)[i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dh[k] = DH[k * N + i];
+                if constexpr (sizeof(T) == 4) dl[k] = DL[k * N + i];
             }
+        }
+        if (MODE != FM_FORCES) {
             const T* V = reinterpret_cast<const T*>(b.v);
             pv[0] = V[i]; pv[1] = V[N + i]; pv[2] = V[2 * N + i];
-            if (S.thermo) {
-                const T4 z = reinterpret_cast<const T4*>(b.xi)[i];
-                pz[0] = z.x; pz[1] = z.y; pz[2] = z.z;
-            }
         }
-        T f[3] = {(T)0, (T)0, (T)0};
-        if (S.pot == POT_SW) {
-            int4* a4 = reinterpret_cast<int4*>(b.lacc) + i;
-            const int4 q = *a4;
-            *a4 = make_int4(0, 0, 0, 0);
-            const T inv = (T)(1.0 / (double)kLegScale);
-            f[0] = (T)q.x * inv; f[1] = (T)q.y * inv; f[2] = (T)q.z * inv;
-        }
+        if (thermo) z = reinterpret_cast<const T4*>(b.xi)[i];
+        if (sw) *a4 = make_int4(0, 0, 0, 0);
+        const T pd[3] = {d0.x + dh[0] + dl[0], d0.y + dh[1] + dl[1], d0.z + dh[2] + dl[2]};
+        const T pz[3] = {z.x, z.y, z.z};
+        const T inv = (T)(1.0 / (double)kLegScale);
+        const T f[3] = {(T)q.x * inv, (T)q.y * inv, (T)q.z * inv};
         finish_atom<T, MODE>(b, S, st, i, f, (T)0, false, pd, pv, pz, s_xm, red);
     }
-    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
+    block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &gst.err);
 }
 
 // FP64 positions and velocities for output, and replacement from FP64 input.
@@ -1680,15 +1782,38 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
     const DevGroup gr = groups[blockIdx.x];
     const int members[2] = {gr.a, gr.b};
     const int nm = gr.b >= 0 ? 2 : 1;
+    // The members' descriptors and states (and the pair's state) are copied into shared memory,
+    // updated there by one thread (a long chain of dependent FP64 steps, each of which would
+    // otherwise wait on global memory), and written back by all threads at the end.
+    __shared__ __align__(16) StagedSys sh[2];
+    __shared__ __align__(16) DevPair spr;
+    {
+        constexpr int ws = (int)(sizeof(DevSys) / 4), wt = (int)(sizeof(DevState) / 4), wp = (int)(sizeof(DevPair) / 4);
+        for (int mi = 0; mi < nm; ++mi) {
+            const uint32_t* gs = reinterpret_cast<const uint32_t*>(b.sys + members[mi]);
+            const uint32_t* gt = reinterpret_cast<const uint32_t*>(b.st + members[mi]);
+            uint32_t* ds = reinterpret_cast<uint32_t*>(&sh[mi].S);
+            uint32_t* dt = reinterpret_cast<uint32_t*>(&sh[mi].st);
+            for (int w = threadIdx.x; w < ws + wt; w += blockDim.x) {
+                if (w < ws) ds[w] = gs[w];
+                else dt[w - ws] = gt[w - ws];
+            }
+        }
+        if (gr.pair >= 0) {
+            const uint32_t* gp = reinterpret_cast<const uint32_t*>(b.pairs + gr.pair);
+            uint32_t* dp = reinterpret_cast<uint32_t*>(&spr);
+            for (int w = threadIdx.x; w < wp; w += blockDim.x) dp[w] = gp[w];
+        }
+    }
+    __syncthreads();
     // decode the slot sums (fixed order: deterministic)
     if (mode != 0) {
         for (int mi = 0; mi < nm; ++mi) {
             const int s = members[mi];
-            DevState& st = b.st[s];
+            DevState& st = sh[mi].st;
             const long long* acc = b.acc + (size_t)s * ACC_N * kSlots;
             if (threadIdx.x < ACC_XI) {
-                long long sum = 0;
-                for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)threadIdx.x * kSlots + sl];
+                const long long sum = slot_sum(acc + (size_t)threadIdx.x * kSlots);
                 const double v = (double)sum / kFix;
                 const int a = threadIdx.x;
                 if (a == ACC_UINT) st.u_int = v;
@@ -1703,10 +1828,10 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
         for (int mi = 0; mi < nm; ++mi) {
             const int s = members[mi];
             if (mode == 0) {
-                const DevSys& S = b.sys[s];
-                DevState& st = b.st[s];
+                const DevSys& S = sh[mi].S;
+                DevState& st = sh[mi].st;
                 if (S.pair >= 0) {
-                    const DevPair& pr = b.pairs[S.pair];
+                    const DevPair& pr = spr;       // a paired system's group is its pair
                     st.lam = 1.0;
                     st.p_tgt = pr.ps;
                 } else if (S.sched != SCHED_NONE) {
@@ -1718,20 +1843,20 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
                 }
                 st.scaled = 0;
             } else {
-                observe(b.sys[s], b.st[s]);
+                observe(sh[mi].S, sh[mi].st);
             }
         }
         if (mode == 1) {
             for (int mi = 0; mi < nm; ++mi) {
                 const int s = members[mi];
-                record_and_kick(b.sys[s], b.st[s], b.dt, b.trace);
+                record_and_kick(sh[mi].S, sh[mi].st, b.dt, b.trace);
             }
             if (gr.pair >= 0) {
-                DevPair& pr = b.pairs[gr.pair];
-                DevState& A = b.st[gr.a];
-                DevState& B = b.st[gr.b];
-                const DevSys& SA = b.sys[gr.a];
-                const DevSys& SB = b.sys[gr.b];
+                DevPair& pr = spr;
+                DevState& A = sh[0].st;
+                DevState& B = sh[1].st;
+                const DevSys& SA = sh[0].S;
+                const DevSys& SB = sh[1].S;
                 const double du = A.u_int / SA.n - B.u_int / SB.n;
                 const double dv = A.V / SA.n - B.V / SB.n;
                 double lam_next, ps_next;
@@ -1762,10 +1887,10 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
                 pr.k += 1;
                 A.lam = B.lam = lam_next;
                 A.p_tgt = B.p_tgt = ps_next;
-                if (pr.err) { atomicOr(&A.err, pr.err); atomicOr(&B.err, pr.err); }
+                if (pr.err) { A.err |= pr.err; B.err |= pr.err; }
             } else {
-                const DevSys& S = b.sys[gr.a];
-                DevState& st = b.st[gr.a];
+                const DevSys& S = sh[0].S;
+                DevState& st = sh[0].st;
                 if (S.sched != SCHED_NONE) {
                     const double lam_next = sched_lambda(S, st.k + 1);
                     st.W += st.dHdl * (lam_next - st.lam);
@@ -1773,16 +1898,28 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
                 }
             }
             for (int mi = 0; mi < nm; ++mi) {
-                const int s = members[mi];
-                DevState& st = b.st[s];
-                prepare_step(b.sys[s], st, b.dt);
+                DevState& st = sh[mi].st;
+                prepare_step(sh[mi].S, st, b.dt);
                 st.rebuild = 0;
                 st.k += 1;
             }
         }
     }
+    __syncthreads();
+    {
+        constexpr int wt = (int)(sizeof(DevState) / 4), wp = (int)(sizeof(DevPair) / 4);
+        for (int mi = 0; mi < nm; ++mi) {
+            uint32_t* gt = reinterpret_cast<uint32_t*>(b.st + members[mi]);
+            const uint32_t* dt = reinterpret_cast<const uint32_t*>(&sh[mi].st);
+            for (int w = threadIdx.x; w < wt; w += blockDim.x) gt[w] = dt[w];
+        }
+        if (gr.pair >= 0) {
+            uint32_t* gp = reinterpret_cast<uint32_t*>(b.pairs + gr.pair);
+            const uint32_t* dp = reinterpret_cast<const uint32_t*>(&spr);
+            for (int w = threadIdx.x; w < wp; w += blockDim.x) gp[w] = dp[w];
+        }
+    }
     if (mode != 2) {
-        __syncthreads();
         for (int mi = 0; mi < nm; ++mi) {
             long long* acc = b.acc + (size_t)members[mi] * ACC_N * kSlots;
             for (int t = threadIdx.x; t < ACC_N * kSlots; t += blockDim.x) acc[t] = 0;
@@ -1823,9 +1960,7 @@ __global__ void k_decode_ev(const long long* acc, double* out7) {
     const int t = threadIdx.x;
     if (t >= 7) return;
     const int a = t == 0 ? ACC_UINT : ACC_VIR + (t - 1);
-    long long sum = 0;
-    for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)a * kSlots + sl];
-    out7[t] = (double)sum / kFix;
+    out7[t] = (double)slot_sum(acc + (size_t)a * kSlots) / kFix;
 }
 
 // ------------------------------------------------------------------------------------
@@ -1886,9 +2021,7 @@ __global__ void k_decode_grad(const long long* acc, double* out8) {
     const int t = threadIdx.x;
     if (t >= 8) return;
     const int a = t == 0 ? ACC_UINT : ACC_DTH + (t - 1);
-    long long sum = 0;
-    for (int sl = 0; sl < kSlots; ++sl) sum += acc[(size_t)a * kSlots + sl];
-    out8[t] = (double)sum / kFix;
+    out8[t] = (double)slot_sum(acc + (size_t)a * kSlots) / kFix;
 }
 
 void launch_decode_grad(const long long* acc, double* out8, cudaStream_t s) {
@@ -1938,13 +2071,16 @@ static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s)
     // an FP64 shell of 32 atoms per block does not fit the 48 KB static shared limit: 4 -> 8
     switch (lanes) {
         case 0:   // one thread per atom, scatter form: FP32 only
-            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
-            else k_edges1<T, true><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
+        case 1: { // one thread per atom: FP32 only (the FP64 columns exceed the shared limit)
+            if constexpr (sizeof(T) == 8) {
+                k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
+            } else {
+                const int items = ntiles * (kTile / kEdges1Threads);
+                if (lanes == 0) k_edges1<T, true><<<items, kEdges1Threads, 0, s>>>(b);
+                else k_edges1<T, false><<<items, kEdges1Threads, 0, s>>>(b);
+            }
             break;
-        case 1:   // one thread per atom: FP32 only (the FP64 columns exceed the shared limit)
-            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
-            else k_edges1<T, false><<<ntiles * (kTile / kEdges1Threads), kEdges1Threads, 0, s>>>(b);
-            break;
+        }
         case 4:
             if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
             else k_edges<T, 4><<<ntiles * 4, kTile, 0, s>>>(b);
