@@ -1177,26 +1177,19 @@ constexpr int kEdges1K1 = kShell1Shared;
 
 // One work item of the thread-per-atom pass A: half a tile (64 atoms).  Every thread of the
 // block calls it with the same item.
-template <typename T, bool SCATTER>
-__device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4<T>::t (*sh_u)[kEdges1Threads],
-                                            T (*sh_r)[kEdges1Threads], typename V4<T>::t* soff) {
+// Pass A for atom i (thread-per-atom): compaction of its Verlet row into the in-cutoff shell
+// (column t of the shared shell table, entries past its K1 rows in the global spill area), pair
+// terms, and the leg forces of the triplets centred on i (stored per shell edge, or in the
+// scatter form added into the force accumulators, with the energy and virial added to red8).
+// pos(j) returns atom j's mirror position (from global memory or a shared copy).
+template <typename T, bool SCATTER, int NT, typename PosFn>
+__device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevState& st,
+                                            const typename V4<T>::t* soff, int i, int t,
+                                            typename V4<T>::t (*sh_u)[NT], T (*sh_r)[NT], PosFn pos,
+                                            T (&red8)[8]) {
     using T4 = typename V4<T>::t;
-    constexpr int NT = kEdges1Threads;
-    // 20 bytes per shell entry and thread (occupancy is bound by this table):
     constexpr int K1 = kShell1Shared, KS = kShell1 - kShell1Shared;
-    const int tile = item / (kTile / NT) + b.tile_base, part = item % (kTile / NT);
-    const TileAtom ta = tile_of(b, tile);
-    const DevSys& S = b.sys[ta.sys];
-    DevState& st = b.st[ta.sys];
-    if (S.pot != POT_SW) return;                 // uniform over the block
-    const SWc<T> P = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
-    offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
-    const int t = threadIdx.x;
-    const int ia = part * NT + t;
-    T red8[8] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};   // scatter form: energy, -, virial
-    if (ia < ta.count) {
-    const int i = ta.first + ia;
-    const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
+    const T4 xi = pos(i);
     const int ci = min(b.cnt[i], b.cap);
     const int* row = b.nbr + (size_t)i * b.cap;
     T4* Fl = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
@@ -1225,7 +1218,7 @@ __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (base + u < ci) xj[u] = reinterpret_cast<const T4*>(b.xs)[e[u] & (int)kIndexMask];
+            if (base + u < ci) xj[u] = pos(e[u] & (int)kIndexMask);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (base + u >= ci) continue;
@@ -1316,8 +1309,8 @@ __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4
     if constexpr (SCATTER) {
         red_force(b.lacc + 4 * (size_t)i, fx, fy, fz, &st.err);
         if (b.e_atom) b.e_atom[i] = (double)en;
-        red8[0] = en;
-        red8[2] = w0; red8[3] = w1; red8[4] = w2; red8[5] = w3; red8[6] = w4; red8[7] = w5;
+        red8[0] += en;
+        red8[2] += w0; red8[3] += w1; red8[4] += w2; red8[5] += w3; red8[6] += w4; red8[7] += w5;
     } else {
         T4* Pa = reinterpret_cast<T4*>(b.P);
         Pa[i] = mk4(fx, fy, fz, en);
@@ -1325,7 +1318,30 @@ __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4
         Pa[b.ntot + 2 * (size_t)i + 1] = mk4(w4, w5, (T)0, (T)0);
     }
     b.shn[i] = m;
-    }   // ia < ta.count
+}
+
+template <typename T, bool SCATTER>
+__device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4<T>::t (*sh_u)[kEdges1Threads],
+                                            T (*sh_r)[kEdges1Threads], typename V4<T>::t* soff) {
+    using T4 = typename V4<T>::t;
+    constexpr int NT = kEdges1Threads;
+    // 20 bytes per shell entry and thread (occupancy is bound by this table):
+    constexpr int K1 = kShell1Shared, KS = kShell1 - kShell1Shared;
+    const int tile = item / (kTile / NT) + b.tile_base, part = item % (kTile / NT);
+    const TileAtom ta = tile_of(b, tile);
+    const DevSys& S = b.sys[ta.sys];
+    DevState& st = b.st[ta.sys];
+    if (S.pot != POT_SW) return;                 // uniform over the block
+    const SWc<T> P = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
+    offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
+    const int t = threadIdx.x;
+    const int ia = part * NT + t;
+    T red8[8] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};   // scatter form: energy, -, virial
+    if (ia < ta.count) {
+        const T4* X = reinterpret_cast<const T4*>(b.xs);
+        edges1_atom<T, SCATTER, kEdges1Threads>(b, P, st, soff, ta.first + ia, t, sh_u, sh_r,
+                                               [X](int j) { return X[j]; }, red8);
+    }
     if constexpr (SCATTER) block_sum_to_acc<T, 8>(red8, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
 }
 
