@@ -1185,8 +1185,8 @@ constexpr int kEdges1K1 = kShell1Shared;
 template <typename T, bool SCATTER, int NT, typename PosFn>
 __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevState& st,
                                             const typename V4<T>::t* soff, int i, int t,
-                                            typename V4<T>::t (*sh_u)[NT], T (*sh_r)[NT], PosFn pos,
-                                            T (&red8)[8]) {
+                                            typename V4<T>::t (*sh_u)[NT], T (*sh_r)[NT], int (*sh_j)[NT],
+                                            PosFn pos, T (&red8)[8]) {
     using T4 = typename V4<T>::t;
     constexpr int K1 = kShell1Shared, KS = kShell1 - kShell1Shared;
     const T4 xi = pos(i);
@@ -1228,7 +1228,10 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
             if (r2 < P.act2) {
                 if (m < capm) {
                     put_u(m, mk4(dx, dy, dz, r2));
-                    Sj[m] = e[u] & (int)kIndexMask;
+                    // the scatter form keeps the shell's atom indices next to it in shared memory
+                    // (global only past its rows); the gather form publishes them for pass B
+                    if (SCATTER && m < K1) sh_j[m][t] = e[u] & (int)kIndexMask;
+                    else Sj[m] = e[u] & (int)kIndexMask;
                 }
                 ++m;
             }
@@ -1238,7 +1241,7 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
         atomicOr(&st.err, NEFE_ERR_SHELL_OVERFLOW);
         m = capm;
     }
-    if (m < kShell) Sj[m] = -1;
+    if (!SCATTER && m < kShell) Sj[m] = -1;
     T fx = 0, fy = 0, fz = 0, en = 0;
     T w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     // Moments of the shell: G = sum_b g_b, m1 = sum_b g_b u_b, M = sum_b g_b u_b u_b^T.  Every
@@ -1296,7 +1299,7 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
         const T ay = k1 * (Muy - c0 * m1y - self * ua.y);
         const T az = k1 * (Muz - c0 * m1z - self * ua.z);
         const T lx = cc * ua.x - ax, ly = cc * ua.y - ay, lz = cc * ua.z - az;
-        if constexpr (SCATTER) red_force(b.lacc + 4 * (size_t)Sj[a], lx, ly, lz, &st.err);
+        if constexpr (SCATTER) red_force(b.lacc + 4 * (size_t)(a < K1 ? sh_j[a][t] : Sj[a]), lx, ly, lz, &st.err);
         else Fl[a] = mk4(lx, ly, lz, (T)0);
         fx -= lx; fy -= ly; fz -= lz;
         en += (T)0.5 * P.epslam * ga * eh;
@@ -1322,7 +1325,8 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
 
 template <typename T, bool SCATTER>
 __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4<T>::t (*sh_u)[kEdges1Threads],
-                                            T (*sh_r)[kEdges1Threads], typename V4<T>::t* soff) {
+                                            T (*sh_r)[kEdges1Threads], int (*sh_j)[kEdges1Threads],
+                                            typename V4<T>::t* soff) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
     // 20 bytes per shell entry and thread (occupancy is bound by this table):
@@ -1339,7 +1343,7 @@ __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4
     T red8[8] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};   // scatter form: energy, -, virial
     if (ia < ta.count) {
         const T4* X = reinterpret_cast<const T4*>(b.xs);
-        edges1_atom<T, SCATTER, kEdges1Threads>(b, P, st, soff, ta.first + ia, t, sh_u, sh_r,
+        edges1_atom<T, SCATTER, kEdges1Threads>(b, P, st, soff, ta.first + ia, t, sh_u, sh_r, sh_j,
                                                [X](int j) { return X[j]; }, red8);
     }
     if constexpr (SCATTER) block_sum_to_acc<T, 8>(red8, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &st.err);
@@ -1350,8 +1354,9 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     using T4 = typename V4<T>::t;
     __shared__ T4 sh_u[kEdges1K1][kEdges1Threads];   // (d, r^2) after compaction, then (u, g)
     __shared__ T sh_r[kEdges1K1][kEdges1Threads];    // r
+    __shared__ int sh_j[SCATTER ? kEdges1K1 : 1][kEdges1Threads];   // shell atom indices (scatter form)
     __shared__ T4 soff[27];
-    edges1_item<T, SCATTER>(b, blockIdx.x, sh_u, sh_r, soff);
+    edges1_item<T, SCATTER>(b, blockIdx.x, sh_u, sh_r, sh_j, soff);
 }
 
 // Force pass B, L lanes per atom:
