@@ -114,6 +114,7 @@ struct DevState {
     float scale_int_f, scale_E_f, thr2_f;
     int scaled;                 // s != 1 on some axis (barostat moved the box this step)
     int hmoved;                 // h != hb on some axis (box differs from the last build)
+    double ibox[3];             // 1 / box at the last list build (set with the grid by k_rebuild_list)
 };
 
 struct DevPair {

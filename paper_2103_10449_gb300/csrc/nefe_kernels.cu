@@ -265,7 +265,13 @@ __device__ void cells_count_tile(const Bufs& b, int tile) {
     DevState& st = b.st[ta.sys];
     __shared__ int s_n3[3];
     __shared__ double s_h[3], s_ib[3];
-    if (threadIdx.x == 0) {                      // the grid of this tile's system, once per tile
+    if (b.rtiles) {                              // engine: the grid was set by k_rebuild_list
+        if (threadIdx.x < 3) {
+            s_n3[threadIdx.x] = st.ncell[threadIdx.x];
+            s_h[threadIdx.x] = st.h[threadIdx.x];
+            s_ib[threadIdx.x] = st.ibox[threadIdx.x];
+        }
+    } else if (threadIdx.x == 0) {               // the grid of this tile's system, once per tile
         int g3[3];
         const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, g3);
         for (int k = 0; k < 3; ++k) {
@@ -348,17 +354,31 @@ __global__ void __launch_bounds__(kTile) k_cells_count(Bufs b) {
     NEFE_FOR_TILES(b, cells_count_tile<T>(b, tile));
 }
 
-// Worklist of the tiles of every system whose rebuild flag is set (all with force_all).
+// Worklist of the tiles of every system whose rebuild flag is set (all with force_all), and the
+// cell grid of each such system at its current box (per axis floor(L/rcs) reduced while
+// L/n < rcs (1 + 1e-9), h = L/n, 1/L), computed once per system here rather than per tile.
 // Tile order in the list does not matter: every tile is processed independently.
 __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
-        if (force_all || b.st[s].rebuild) {
+        DevState& st = b.st[s];
+        if (force_all || st.rebuild) {
             const DevSys& S = b.sys[s];
             const int base = atomicAdd(&cnt, S.ntile);
             for (int t = 0; t < S.ntile; ++t) b.rtiles[base + t] = S.tile0 + t;
+            int g3[3];
+            const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, g3);
+            for (int k = 0; k < 3; ++k) {
+                st.ncell[k] = g3[k];
+                st.h[k] = __ddiv_rn(st.box[k], (double)g3[k]);
+                st.hb[k] = st.h[k];
+                st.ibox[k] = __ddiv_rn(1.0, st.box[k]);
+            }
+            refresh_box_f(st);
+            st.nbuild += 1;
+            if (!ok) atomicOr(&st.err, NEFE_ERR_BOX);
         }
     }
     __syncthreads();
@@ -616,7 +636,7 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(kTile) k_nlist(Bufs b) {
+__global__ void __launch_bounds__(kTile, 5) k_nlist(Bufs b) {
     constexpr int G = kTile / L;
     __shared__ int buf[G][kMaxCap + 1];   // padded: the groups of a warp on different banks
     __shared__ int cnt_s[G];
