@@ -115,6 +115,7 @@ struct DevState {
     int scaled;                 // s != 1 on some axis (barostat moved the box this step)
     int hmoved;                 // h != hb on some axis (box differs from the last build)
     double ibox[3];             // 1 / box at the last list build (set with the grid by k_rebuild_list)
+    double gbox[3], grcs;       // box and list radius the cell grid was computed for (0: never)
 };
 
 struct DevPair {

@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(kTile) k_cells_count(Bufs b) {
 
 // Worklist of the tiles of every system whose rebuild flag is set (all with force_all), and the
 // cell grid of each such system at its current box (per axis floor(L/rcs) reduced while
-// L/n < rcs (1 + 1e-9), h = L/n, 1/L), computed once per system here rather than per tile.
+// L/n < rcs (1 + 1e-9), h = L/n, 1/L), computed once per system here rather than per tile, and
+// only when the box or the list radius differ from the ones the grid was last computed for
+// (the FP64 divisions are skipped for every system at fixed volume).
 // Tile order in the list does not matter: every tile is processed independently.
 __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
     __shared__ int cnt;
@@ -368,25 +370,34 @@ __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int forc
             const DevSys& S = b.sys[s];
             const int base = atomicAdd(&cnt, S.ntile);
             for (int t = 0; t < S.ntile; ++t) b.rtiles[base + t] = S.tile0 + t;
-            int g3[3];
-            const bool ok = grid_for(st.box, S.rcs, S.ncell_cap, g3);
-            for (int k = 0; k < 3; ++k) {
-                st.ncell[k] = g3[k];
-                st.h[k] = __ddiv_rn(st.box[k], (double)g3[k]);
-                st.hb[k] = st.h[k];
-                st.ibox[k] = __ddiv_rn(1.0, st.box[k]);
+            const double bx[3] = {st.box[0], st.box[1], st.box[2]};
+            const bool same = st.grcs == S.rcs && st.gbox[0] == bx[0] && st.gbox[1] == bx[1] &&
+                              st.gbox[2] == bx[2];
+            if (!same) {
+                int g3[3];
+                const bool ok = grid_for(bx, S.rcs, S.ncell_cap, g3);
+                for (int k = 0; k < 3; ++k) {
+                    st.ncell[k] = g3[k];
+                    st.h[k] = __ddiv_rn(bx[k], (double)g3[k]);
+                    st.hb[k] = st.h[k];
+                    st.ibox[k] = __ddiv_rn(1.0, bx[k]);
+                    st.gbox[k] = bx[k];
+                }
+                st.grcs = S.rcs;
+                refresh_box_f(st);
+                if (!ok) atomicOr(&st.err, NEFE_ERR_BOX);
             }
-            refresh_box_f(st);
             st.nbuild += 1;
-            if (!ok) atomicOr(&st.err, NEFE_ERR_BOX);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) *b.rcount = cnt;
 }
 
-// R2: exclusive scan of the occupancy (one 256-thread block per system); resets counts.
+// R2: exclusive scan of the occupancy (one 256-thread block per system, 8 consecutive cells
+// per thread, so one pass covers 2048 cells); resets counts.
 __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
+    constexpr int PT = 8;
     const int s = blockIdx.x;
     const DevSys& S = b.sys[s];
     DevState& st = b.st[s];
@@ -396,14 +407,17 @@ __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
     int* count = b.cell_count + S.cell0;
     int* cursor = b.cell_cursor + S.cell0;
     __shared__ int warp_tot[8];
-    __shared__ int carry_s;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int base = 0; base < ncells; base += 256) {
-        const int idx = base + threadIdx.x;
-        const int c = idx < ncells ? count[idx] : 0;
-        int incl = c;
+    int carry = 0;
+    for (int base = 0; base < ncells; base += 256 * PT) {
+        const int c0 = base + (int)threadIdx.x * PT;
+        int v[PT], tsum = 0;
+#pragma unroll
+        for (int u = 0; u < PT; ++u) {
+            v[u] = c0 + u < ncells ? count[c0 + u] : 0;
+            tsum += v[u];
+        }
+        int incl = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -416,20 +430,22 @@ __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
             if (k < w) woff += warp_tot[k];
             tot += warp_tot[k];
         }
-        const int carry = carry_s;
-        if (idx < ncells) {
-            const int excl = carry + woff + incl - c;
-            start[idx] = excl;
-            cursor[idx] = excl;
-            count[idx] = 0;
+        int run = carry + woff + incl - tsum;
+#pragma unroll
+        for (int u = 0; u < PT; ++u) {
+            if (c0 + u < ncells) {
+                start[c0 + u] = run;
+                cursor[c0 + u] = run;
+                count[c0 + u] = 0;
+            }
+            run += v[u];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) carry_s = carry + tot;
-        __syncthreads();
+        carry += tot;
+        __syncthreads();                         // warp_tot is rewritten by the next pass
     }
     if (threadIdx.x == 0) {
-        start[ncells] = carry_s;
-        if (carry_s != S.n) atomicOr(&st.err, NEFE_ERR_CELL);
+        start[ncells] = carry;
+        if (carry != S.n) atomicOr(&st.err, NEFE_ERR_CELL);
     }
 }
 
@@ -499,33 +515,66 @@ __device__ __noinline__ bool exact_pair_in(const Bufs& b, const double box[3], i
     return rr < rcs2;
 }
 
-// R5: Verlet list, L lanes per atom.  Lane l walks neighbour cells l, l + L, ... (cell
-// offset o in {-1,0,1}^3) and their atoms, which sit contiguously in the cell-ordered mirror
-// copy.  A candidate is accepted or rejected on its mirror distance when that lies outside a
-// relative band of 1e-4 (FP32) / 1e-10 (FP64) around rcs^2, and inside the band by the exact
-// FP64 criterion (which must also agree with the offset's image), so the list equals the
-// plain definition bit for bit.  Accepted entries are appended in any order (a shared
-// counter) and then ranked by atom index into the row, which fixes the order.
+// R5: Verlet list, L lanes per atom (a group of L lanes of one warp).
+// The 27 neighbour cells of atom i's cell form 9 x-rows (one per (oy, oz)); the three cells of
+// a row (ox = -1, 0, 1) are consecutive in the cell-ordered mirror copy unless the row wraps at
+// the box edge (cx = 0 or cx = nx - 1), so a row is one contiguous range of candidates (two
+// pieces where it wraps).  A cell whose box is farther than rcs from atom i is pruned, which
+// trims a row at its ends or drops it.  The pieces are concatenated into one candidate sequence
+// of the group, which its lanes walk L at a time (lane l takes candidates l, l + L, ...: every
+// lane but the last pass's is busy); the cell offset of a candidate follows from its position
+// against its piece's cell boundaries.  A candidate is accepted or rejected on its mirror
+// distance when that lies outside a relative band of 1e-4 (FP32) / 1e-10 (FP64) around rcs^2,
+// and inside the band by the exact FP64 criterion (which must also agree with the offset's
+// image), so the list equals the plain definition bit for bit.  Accepted entries are appended
+// through a ballot, as keys j * 32 + o, and then ranked by atom index into the row, which
+// fixes the order.
 constexpr int kRebuildBlocks = 152 * 8;   // bounded grid of the worklist-driven rebuild kernels
+constexpr int kRowPieces = 18;            // piece p of row r at 2 r + p
+constexpr int kKeyRow = kMaxCap + 4;      // key buffer row: 16-byte aligned, groups on different banks
+
+// Per-group tables of the list build in shared memory.
+template <typename T>
+struct NlistShared {
+    using T4 = typename V4<T>::t;
+    int4 pc[kRowPieces];          // (first candidate in xcs, start of its 2nd cell, of its 3rd cell, first flat index)
+    T4 ps[kRowPieces];            // (x_i - ox h_x, y_i - oy h_y, z_i - oz h_z) of the piece's first cell
+    int code[kRowPieces];         // cell-offset code of the piece's first cell
+    int flat_end;                 // number of candidates of the group
+};
+
+// One piece of row (oy, oz): cells x0 .. x0 + nc - 1 of the row starting at rb (consecutive in
+// memory), as (first candidate, end, start of the second cell, start of the third cell), the
+// last two INT_MAX when absent.
+__device__ __forceinline__ int4 row_piece(const int* start, int rb, int x0, int nc, int n) {
+    const int lo = max(0, min(start[rb + x0], n));
+    const int hi = max(lo, min(start[rb + x0 + nc], n));
+    const int b1 = nc > 1 ? start[rb + x0 + 1] : INT_MAX;
+    const int b2 = nc > 2 ? start[rb + x0 + 2] : INT_MAX;
+    return make_int4(lo, hi, b1, b2);
+}
+
 template <typename T, int L>
-__device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap + 1], int* cnt_s) {
+__device__ void nlist_item(const Bufs& b, int tile, int part, unsigned (*keys)[kKeyRow],
+                           NlistShared<T>* tab) {
     using T4 = typename V4<T>::t;
     constexpr int G = kTile / L;
+    constexpr int RR = (9 + L - 1) / L;          // rows per lane
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
-    DevState& st = b.st[ta.sys];
-    DevState& gst = st;
-    const int lane = threadIdx.x % L, grp = threadIdx.x / L;
-    const int lbase = ((threadIdx.x & 31) / L) * L;
-    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << lbase);
-    const int ia = part * G + grp;
-    const bool valid = ia < ta.count;
-    const int i = ta.first + ia;
-    if (!valid) return;                          // whole group leaves together
     if (S.pot != POT_SW) {                       // no SW term: no SW list (uniform over the block)
-        if (lane == 0) b.cnt[i] = 0;
+        const int ia = part * G + (int)threadIdx.x / L;
+        if (threadIdx.x % L == 0 && ia < ta.count) b.cnt[ta.first + ia] = 0;
         return;
     }
+    DevState& st = b.st[ta.sys];
+    const int lane = threadIdx.x % L, grp = threadIdx.x / L;
+    const int lbase = ((threadIdx.x & 31) / L) * L;
+    NlistShared<T>& sh = tab[grp];
+    const int ia = part * G + grp;
+    // groups past the tile's end stay in the warp-uniform loops below with no candidates
+    const bool valid = ia < ta.count;
+    const int i = ta.first + (valid ? ia : 0);
     const int nx = st.ncell[0], ny = st.ncell[1], nz = st.ncell[2];
     const int cell = b.cell_of[i];
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
@@ -540,64 +589,94 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
         lo2 = S.rcs * S.rcs * (1.0 - 1e-10);
         hi2 = S.rcs * S.rcs * (1.0 + 1e-10);
     }
-    // A cell whose box is farther than rcs from atom i (the mirror lies in [0, h) of its own
-    // cell) holds no neighbour and is skipped; the bound is relaxed by 1e-3 of rcs^2, far
-    // above the rounding of the mirror positions, so no pair within rcs can be missed.
+    // pruning bound: relaxed by 1e-3 of rcs^2, far above the rounding of the mirror positions
+    // (which lie in [0, h) of their own cell), so no pair within rcs can be missed
     const T prune2 = (T)(S.rcs * S.rcs * 1.001);
     const T4* xc = reinterpret_cast<const T4*>(b.xcs) + S.off;
-    if (lane == 0) cnt_s[grp] = 0;
-    __syncwarp(gmask);
-    // the lane's cells o = lane, lane + L, ...: every range is loaded first (independent
-    // loads in flight), then each range is walked VB candidates at a time (FP32: 4; FP64: 2,
-    // which keeps the wider positions in registers)
-    constexpr int KC = (27 + L - 1) / L;
-    constexpr int VB = sizeof(T) == 4 ? 4 : 2;
-    int lo_[KC], hi_[KC];
+    // first ox of a row's second piece: the row wraps between ox = -1 and 0 (cx = 0) or between
+    // 0 and +1 (cx = nx - 1); 2 when it does not wrap (nx >= 2, so never both)
+    const int brk = cx == 0 ? 0 : (cx == nx - 1 ? 1 : 2);
+    int carry = 0;
 #pragma unroll
-    for (int k = 0; k < KC; ++k) {
-        const int o = lane + k * L;
-        lo_[k] = 0;
-        hi_[k] = 0;
-        if (o >= 27) continue;
-        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-        const T ex = ox < 0 ? xi.x : (ox > 0 ? hx - xi.x : (T)0);
-        const T ey = oy < 0 ? xi.y : (oy > 0 ? hy - xi.y : (T)0);
-        const T ez = oz < 0 ? xi.z : (oz > 0 ? hz - xi.z : (T)0);
-        const T fx = ex > (T)0 ? ex : (T)0, fy = ey > (T)0 ? ey : (T)0, fz = ez > (T)0 ? ez : (T)0;
-        if (fx * fx + fy * fy + fz * fz > prune2) continue;
-        int xx = cx + ox, yy = cy + oy, zz = cz + oz;
-        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-        const int c2 = xx + nx * (yy + ny * zz);
-        lo_[k] = start[c2];
-        hi_[k] = start[c2 + 1];
-    }
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-        const int o = lane + k * L;
-        const int lo = max(0, min(lo_[k], S.n)), hi = max(lo, min(hi_[k], S.n));
-        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-        const T offx = (T)ox * hx, offy = (T)oy * hy, offz = (T)oz * hz;
-        for (int p0 = lo; p0 < hi; p0 += VB) {
-            T4 xj[VB];
-#pragma unroll
-            for (int u = 0; u < VB; ++u)
-                if (p0 + u < hi) xj[u] = xc[p0 + u];
-#pragma unroll
-            for (int u = 0; u < VB; ++u) {
-                if (p0 + u >= hi) break;
-                const int j = unpack_index(xj[u].w);
-                if (j < S.off || j >= S.off + S.n) {
-                    atomicOr(&gst.err, NEFE_ERR_CELL);
-                    continue;
+    for (int k = 0; k < RR; ++k) {
+        const int r = lane + k * L;
+        int4 p0 = make_int4(0, 0, INT_MAX, INT_MAX), p1 = p0;
+        int a = 0, a2 = 0, cb = 0;
+        if (valid && r < 9) {
+            const int oy = r % 3 - 1, oz = r / 3 - 1;
+            const T ey = oy < 0 ? xi.y : (oy > 0 ? hy - xi.y : (T)0);
+            const T ez = oz < 0 ? xi.z : (oz > 0 ? hz - xi.z : (T)0);
+            const T fy = ey > (T)0 ? ey : (T)0, fz = ez > (T)0 ? ez : (T)0;
+            const T fyz = fy * fy + fz * fz;
+            cb = 3 * (oy + 1) + 9 * (oz + 1);
+            if (fyz <= prune2) {
+                const T fl = xi.x > (T)0 ? xi.x : (T)0, fr = hx - xi.x > (T)0 ? hx - xi.x : (T)0;
+                a = fl * fl + fyz <= prune2 ? -1 : 0;          // lower cell kept
+                const int e = fr * fr + fyz <= prune2 ? 1 : 0; // upper cell kept
+                int yy = cy + oy, zz = cz + oz;
+                yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+                zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+                const int rb = nx * (yy + ny * zz);
+                const int e1 = min(e, brk - 1);               // first piece: ox = a .. e1
+                if (a <= e1) {
+                    int x0 = cx + a;
+                    x0 = x0 < 0 ? x0 + nx : x0;
+                    p0 = row_piece(start, rb, x0, e1 - a + 1, S.n);
                 }
-                if (j == i && o == 13) continue;
-                const T dx = xj[u].x - xi.x + offx;
-                const T dy = xj[u].y - xi.y + offy;
-                const T dz = xj[u].z - xi.z + offz;
-                const T dd = dx * dx + dy * dy + dz * dz;
-                bool in = false;
+                a2 = max(a, brk);                             // second piece: ox = a2 .. e
+                if (brk < 2 && a2 <= e) {
+                    int x0 = cx + a2;
+                    x0 = x0 >= nx ? x0 - nx : x0;
+                    p1 = row_piece(start, rb, x0, e - a2 + 1, S.n);
+                }
+            }
+            const T yo = xi.y - (T)oy * hy, zo = xi.z - (T)oz * hz;
+            sh.ps[2 * r] = mk4(xi.x - (T)a * hx, yo, zo, (T)0);
+            sh.ps[2 * r + 1] = mk4(xi.x - (T)a2 * hx, yo, zo, (T)0);
+            sh.code[2 * r] = cb + a + 1;
+            sh.code[2 * r + 1] = cb + a2 + 1;
+        }
+        // flat positions: exclusive scan of the rows' lengths over the group, row order
+        const int n0 = p0.y - p0.x, len = n0 + (p1.y - p1.x);
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o, L);
+            if (lane >= o) incl += y;
+        }
+        const int f0 = carry + incl - len;
+        if (valid && r < 9) {
+            sh.pc[2 * r] = make_int4(p0.x, p0.z, p0.w, f0);
+            sh.pc[2 * r + 1] = make_int4(p1.x, p1.z, p1.w, f0 + n0);
+        }
+        carry += __shfl_sync(0xffffffffu, incl, L - 1, L);
+    }
+    if (lane == 0) sh.flat_end = carry;
+    __syncwarp();
+    // walk the flat sequence L candidates at a time; the pass count is uniform over the warp
+    const int total = carry;
+    const int npass = __reduce_max_sync(0xffffffffu, (total + L - 1) / L);
+    int e = 0, cnt = 0;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int t = pass * L + lane;
+        bool in = false;
+        unsigned key = 0u;
+        if (t < total) {
+            while (e + 1 < kRowPieces && t >= sh.pc[e + 1].w) ++e;   // entries in flat order
+            const int4 pc = sh.pc[e];
+            const T4 po = sh.ps[e];
+            const int p = pc.x + (t - pc.w);
+            const T4 xj = xc[p];
+            const int j = unpack_index(xj.w);
+            const int inc = (p >= pc.y ? 1 : 0) + (p >= pc.z ? 1 : 0);
+            const int o = sh.code[e] + inc;
+            const T dx = (xj.x - po.x) + (T)inc * hx;
+            const T dy = xj.y - po.y;
+            const T dz = xj.z - po.z;
+            const T dd = dx * dx + dy * dy + dz * dz;
+            if ((unsigned)(j - S.off) >= (unsigned)S.n) {
+                atomicOr(&st.err, NEFE_ERR_CELL);
+            } else if (!(j == i && o == 13)) {
                 if (dd < lo2) {
                     in = true;
                 } else if (dd <= hi2) {
@@ -607,47 +686,71 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, int (*buf)[kMaxCap
                          fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
                          fabs(d[2] - (double)dz) < 0.5 * st.h[2];
                 }
-                if (in) {
-                    const int pos = atomicAdd(&cnt_s[grp], 1);
-                    if (pos < kMaxCap) buf[grp][pos] = j | (o << kCodeShift);
-                }
+            }
+            key = (unsigned)j * 32u + (unsigned)o;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        const unsigned m = (L == 32) ? bal : ((bal >> lbase) & ((1u << L) - 1u));
+        if (in) {
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (pos < kMaxCap) keys[grp][pos] = key;
+        }
+        cnt += __popc(m);
+    }
+    // rank by atom index into the row (indices in a row are distinct); the key row is padded to
+    // a multiple of 4 with the largest key, so it is read 4 keys at a time
+    const int have = cnt < kMaxCap ? cnt : kMaxCap;
+    const int have4 = (have + 3) & ~3;
+    for (int z = have + lane; z < have4; z += L) keys[grp][z] = 0xffffffffu;
+    __syncwarp();
+    if (valid) {
+        const int cap = b.cap;
+        const int mrow = cnt < cap ? cnt : cap;
+        int* out = b.nbr + (size_t)i * cap;
+        const uint4* row4 = reinterpret_cast<const uint4*>(keys[grp]);
+        constexpr int R = 4;
+        for (int a0 = 0; a0 < have; a0 += R * L) {
+            unsigned k[R];
+            int rk[R];
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int a = a0 + u * L + lane;
+                k[u] = a < have ? keys[grp][a] : 0xffffffffu;
+                rk[u] = 0;
+            }
+            for (int z = 0; z < have4; z += 4) {
+                const uint4 v = row4[z >> 2];
+#pragma unroll
+                for (int u = 0; u < R; ++u)
+                    rk[u] += (v.x < k[u] ? 1 : 0) + (v.y < k[u] ? 1 : 0) + (v.z < k[u] ? 1 : 0) +
+                             (v.w < k[u] ? 1 : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int a = a0 + u * L + lane;
+                if (a < have && rk[u] < mrow) out[rk[u]] = (int)((k[u] >> 5) | ((k[u] & 31u) << kCodeShift));
             }
         }
+        if (lane == 0) {
+            b.cnt[i] = cnt;
+            if (cnt > cap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
+        }
     }
-    __syncwarp(gmask);
-    const int count = cnt_s[grp];
-    const int cap = b.cap;
-    // rank by atom index into the row (indices in a row are distinct)
-    const int m = count < cap ? count : cap;
-    const int have = count < kMaxCap ? count : kMaxCap;
-    int* out = b.nbr + (size_t)i * cap;
-    for (int a = lane; a < have; a += L) {
-        const int e = buf[grp][a];
-        const int key = e & (int)kIndexMask;
-        int r = 0;
-        for (int z = 0; z < have; ++z) r += ((buf[grp][z] & (int)kIndexMask) < key) ? 1 : 0;
-        if (r < m) out[r] = e;
-    }
-    if (lane == 0) {
-        b.cnt[i] = count;
-        if (count > cap) atomicOr(&gst.err, NEFE_ERR_NBR_OVERFLOW);
-    }
-    __syncwarp(gmask);                           // shared tables reused by the next item
+    __syncwarp();                                // shared tables reused by the next item
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(kTile, 5) k_nlist(Bufs b) {
+__global__ void __launch_bounds__(kTile, 8) k_nlist(Bufs b) {
     constexpr int G = kTile / L;
-    __shared__ int buf[G][kMaxCap + 1];   // padded: the groups of a warp on different banks
-    __shared__ int cnt_s[G];
+    __shared__ __align__(16) unsigned keys[G][kKeyRow];
+    __shared__ NlistShared<T> tab[G];
     if (b.rtiles) {
         const int n = *b.rcount * L;
-        for (int w = blockIdx.x; w < n; w += gridDim.x) nlist_item<T, L>(b, b.rtiles[w / L], w % L, buf, cnt_s);
+        for (int w = blockIdx.x; w < n; w += gridDim.x) nlist_item<T, L>(b, b.rtiles[w / L], w % L, keys, tab);
     } else {
-        nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, buf, cnt_s);
+        nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, keys, tab);
     }
 }
-
 // ------------------------------------------------------------------------------------
 // Uhlenbeck-Ford fluid (the liquid's reference system, Sec. 2.1):
 //   u(r) = -p kT ln(1 - exp(-r^2/sigma^2)) - u(rc),  r < rc.
