@@ -416,7 +416,7 @@ NEFE_API int nefe_set_tuning(nefe_ctx* ctx, int lanes_per_atom);
 NEFE_API int nefe_get_lanes(nefe_ctx* ctx, int lanes[3]);
 /* Fixes pass B's lanes per atom (1, 2, 4 or 8). */
 NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
-/* Fixes the list build's lanes per atom (8, 16 or 32). */
+/* Fixes the list build's form: 0 = one warp per cell (the default), or 8, 16, 32 lanes per atom. */
 NEFE_API int nefe_set_list_tuning(nefe_ctx* ctx, int lanes_per_atom);
 
 /* Batched state transfer for every system at once: host (Ntot, 3) arrays, systems in the

@@ -68,7 +68,7 @@ struct nefe_ctx {
     void *d_v = nullptr, *d_dhi = nullptr, *d_dlo = nullptr;
     void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_xcs = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
     void *d_shd = nullptr, *d_P = nullptr, *d_spill = nullptr;
-    int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr;
+    int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr, *d_rcbase = nullptr;
     int *d_uf_nbr = nullptr, *d_uf_cnt = nullptr, *d_uf_tiles = nullptr;
     int* d_lacc = nullptr;   // scatter-form force accumulators (FP32 contexts)
     void* d_uf_F = nullptr;
@@ -84,7 +84,7 @@ struct nefe_ctx {
     int lanes = 8;           // pass A lanes per atom (1 = one thread per atom, 4, 8, 16, 32; 0 = one
                              // thread per atom in the scatter form, whose pass B is k_finish)
     int glanes = 4;          // pass B lanes per atom (1, 2, 4, 8)
-    int llanes = 8;          // list-build lanes per atom (8, 16, 32)
+    int llanes = 0;          // list build: 0 one warp per cell; 8, 16, 32 lanes per atom
     double tune_us = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -407,6 +407,7 @@ int setup(nefe_ctx* c) {
     }
     if ((rc = dalloc(c, &c->d_rtiles, sizeof(int) * tile_sys.size()))) return rc;
     if ((rc = dalloc(c, &c->d_rcount, sizeof(int)))) return rc;
+    if ((rc = dalloc(c, &c->d_rcbase, sizeof(int) * (size_t)(nsys + 1)))) return rc;
     if ((rc = dalloc(c, &c->d_q, sizeof(int4) * N))) return rc;
     if ((rc = dalloc(c, &c->d_cell_of, sizeof(int) * N))) return rc;
     if ((rc = dalloc(c, &c->d_perm, sizeof(int) * N))) return rc;
@@ -473,7 +474,7 @@ int setup(nefe_ctx* c) {
     b.x = c->d_x; b.v = c->d_v; b.dhi = c->d_dhi; b.dlo = c->d_dlo; b.r0 = c->d_r0; b.F = c->d_F;
     b.xs = c->d_xs; b.xa = c->d_xa; b.xcs = c->d_xcs; b.sd0 = c->d_sd0; b.xi = c->d_xi;
     b.shd = c->d_shd; b.shj = c->d_shj; b.shn = c->d_shn; b.P = c->d_P; b.spill = c->d_spill;
-    b.rtiles = c->d_rtiles; b.rcount = c->d_rcount;
+    b.rtiles = c->d_rtiles; b.rcount = c->d_rcount; b.rcbase = c->d_rcbase;
     b.q = c->d_q; b.cell_of = c->d_cell_of; b.perm = c->d_perm; b.cell_start = c->d_cell_start;
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;
@@ -972,7 +973,7 @@ static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>
     // then the list build's lanes with the chosen pair (its cost is only seen in real steps,
     // where a few systems rebuild at a time)
     int best_l = c->llanes;
-    for (int ll : {8, 16, 32}) {
+    for (int ll : {0, 8, 16, 32}) {
         if (rc != NEFE_OK || ll == best_l) continue;
         c->lanes = best_a;
         c->glanes = best_b;
@@ -1314,8 +1315,8 @@ int nefe_set_gather_tuning(nefe_ctx* c, int lanes) {
 
 int nefe_set_list_tuning(nefe_ctx* c, int lanes) {
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
-    if (lanes != 8 && lanes != 16 && lanes != 32)
-        return fail(NEFE_EINVAL, "the list build supports 8, 16 or 32 lanes per atom");
+    if (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(NEFE_EINVAL, "the list build takes 0 (one warp per cell) or 8, 16, 32 lanes per atom");
     if (lanes != c->llanes) drop_graph(c);
     c->llanes = lanes;
     c->b.list_lanes = lanes;

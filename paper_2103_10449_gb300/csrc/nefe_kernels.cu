@@ -392,6 +392,36 @@ __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int forc
     }
     __syncthreads();
     if (threadIdx.x == 0) *b.rcount = cnt;
+    if (b.rcbase) {   // first worklist cell of each system: exclusive scan of the flagged cell counts
+        __shared__ int wsum[8];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int carry = 0;
+        for (int base = 0; base < nsys; base += 256) {
+            const int s = base + (int)threadIdx.x;
+            int v = 0;
+            if (s < nsys) {
+                const DevState& st = b.st[s];
+                if (force_all || st.rebuild) v = st.ncell[0] * st.ncell[1] * st.ncell[2];
+            }
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) wsum[w] = incl;
+            __syncthreads();
+            int woff = 0, tot = 0;
+            for (int k = 0; k < 8; ++k) {
+                if (k < w) woff += wsum[k];
+                tot += wsum[k];
+            }
+            if (s < nsys) b.rcbase[s] = carry + woff + incl - v;
+            carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) b.rcbase[nsys] = carry;
+    }
 }
 
 // R2: exclusive scan of the occupancy (one 256-thread block per system, 8 consecutive cells
@@ -656,45 +686,51 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, unsigned (*keys)[k
     // walk the flat sequence L candidates at a time; the pass count is uniform over the warp
     const int total = carry;
     const int npass = __reduce_max_sync(0xffffffffu, (total + L - 1) / L);
-    int e = 0, cnt = 0;
+    int cnt = 0;
     for (int pass = 0; pass < npass; ++pass) {
         const int t = pass * L + lane;
-        bool in = false;
+        bool in = false, band = false, bad = false;
         unsigned key = 0u;
-        if (t < total) {
-            while (e + 1 < kRowPieces && t >= sh.pc[e + 1].w) ++e;   // entries in flat order
+        T dx = (T)0, dy = (T)0, dz = (T)0;
+        int j = 0;
+        if (t < total) {                         // straight-line: no branch inside
+            int e = 0;                           // piece of t: last entry whose flat start is <= t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int c = e + step;
+                if (c < kRowPieces && sh.pc[c].w <= t) e = c;
+            }
             const int4 pc = sh.pc[e];
             const T4 po = sh.ps[e];
             const int p = pc.x + (t - pc.w);
             const T4 xj = xc[p];
-            const int j = unpack_index(xj.w);
+            j = unpack_index(xj.w);
             const int inc = (p >= pc.y ? 1 : 0) + (p >= pc.z ? 1 : 0);
             const int o = sh.code[e] + inc;
-            const T dx = (xj.x - po.x) + (T)inc * hx;
-            const T dy = xj.y - po.y;
-            const T dz = xj.z - po.z;
+            dx = (xj.x - po.x) + (T)inc * hx;
+            dy = xj.y - po.y;
+            dz = xj.z - po.z;
             const T dd = dx * dx + dy * dy + dz * dz;
-            if ((unsigned)(j - S.off) >= (unsigned)S.n) {
-                atomicOr(&st.err, NEFE_ERR_CELL);
-            } else if (!(j == i && o == 13)) {
-                if (dd < lo2) {
-                    in = true;
-                } else if (dd <= hi2) {
-                    double d[3];
-                    in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
-                    in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
-                         fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
-                         fabs(d[2] - (double)dz) < 0.5 * st.h[2];
-                }
-            }
+            bad = (unsigned)(j - S.off) >= (unsigned)S.n;
+            const bool cand = !bad && !(j == i && o == 13);
+            in = cand && dd < lo2;
+            band = cand && !(dd < lo2) && dd <= hi2;
             key = (unsigned)j * 32u + (unsigned)o;
+        }
+        if (__any_sync(0xffffffffu, bad || band)) {   // rare: a corrupt cell table or the exact test
+            if (bad) atomicOr(&st.err, NEFE_ERR_CELL);
+            if (band) {
+                double d[3];
+                in = exact_pair_in(b, st.box, i, j, __dmul_rn(S.rcs, S.rcs), d);
+                in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
+                     fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
+                     fabs(d[2] - (double)dz) < 0.5 * st.h[2];
+            }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, in);
         const unsigned m = (L == 32) ? bal : ((bal >> lbase) & ((1u << L) - 1u));
-        if (in) {
-            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (pos < kMaxCap) keys[grp][pos] = key;
-        }
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (in && pos < kMaxCap) keys[grp][pos] = key;
         cnt += __popc(m);
     }
     // rank by atom index into the row (indices in a row are distinct); the key row is padded to
@@ -751,6 +787,219 @@ __global__ void __launch_bounds__(kTile, 8) k_nlist(Bufs b) {
         nlist_item<T, L>(b, blockIdx.x / L, blockIdx.x % L, keys, tab);
     }
 }
+
+// R5 (list mode 0, the default): one warp per cell.  The atoms of a cell share its 27 neighbour
+// cells, so the warp walks that candidate sequence once (its 9 x-rows as pieces, 32 candidates
+// at a time, one per lane: position, image offset and index loaded once) and tests every
+// candidate against each atom of the cell in turn (the cell's atoms up to 16 at a time, their
+// positions in shared memory), with the same filter, band and exact test as above.  A ballot
+// per cell atom appends its accepted keys j * 32 + o to its shared row (the count of cell atom a
+// lives in lane a), and the rows are then ranked by atom index, one key per lane.  Every
+// candidate position is read once per neighbouring cell instead of once per neighbouring atom.
+constexpr int kHomeChunk = 8;             // cell atoms per walk of the candidate sequence
+template <typename T>
+struct CellListShared {
+    using T4 = typename V4<T>::t;
+    unsigned keys[kHomeChunk][kKeyRow];   // accepted keys of each cell atom
+    T4 home[kHomeChunk];                  // cell atoms: mirror position, index in .w
+    int4 pc[kRowPieces];                  // (first candidate, start of 2nd cell, of 3rd cell, first flat index)
+    T4 po[kRowPieces];                    // offset (ox h_x, oy h_y, oz h_z) of the piece's first cell
+    int code[kRowPieces];                 // cell-offset code of the piece's first cell
+};
+
+template <typename T>
+__device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellListShared<T>& sh, int lane) {
+    using T4 = typename V4<T>::t;
+    constexpr unsigned kAll = 0xffffffffu;
+    const DevSys& S = b.sys[s];
+    DevState& st = b.st[s];
+    const int* start = b.cell_start + S.cell0 + s;
+    const int n = S.n, off = S.off;
+    const int hs = max(0, min(start[c], n)), he = max(hs, min(start[c + 1], n));
+    const int m = he - hs;
+    if (m == 0) return;
+    const T4* xc = reinterpret_cast<const T4*>(b.xcs) + off;
+    if (S.pot != POT_SW) {                       // no SW term: no SW list
+        for (int q = lane; q < m; q += 32) {
+            const int i = unpack_index(xc[hs + q].w);
+            if ((unsigned)(i - off) < (unsigned)n) b.cnt[i] = 0;
+        }
+        return;
+    }
+    const int nx = st.ncell[0], ny = st.ncell[1], nz = st.ncell[2];
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    const T hx = pick<T>(st.h[0], st.h_f[0]), hy = pick<T>(st.h[1], st.h_f[1]), hz = pick<T>(st.h[2], st.h_f[2]);
+    T lo2, hi2;
+    if constexpr (sizeof(T) == 4) {
+        lo2 = S.rcs2_lo_f;
+        hi2 = S.rcs2_hi_f;
+    } else {
+        lo2 = S.rcs * S.rcs * (1.0 - 1e-10);
+        hi2 = S.rcs * S.rcs * (1.0 + 1e-10);
+    }
+    // the rows: lane r < 9 builds row r = (oy, oz) as one piece (ox = -1 .. 1), or two where it
+    // wraps at the box edge (cx = 0: the piece ox = -1, then 0 .. 1; cx = nx - 1: -1 .. 0, then 1)
+    const int brk = cx == 0 ? 0 : (cx == nx - 1 ? 1 : 2);
+    int len = 0, n0 = 0;
+    int4 p0 = make_int4(0, 0, INT_MAX, INT_MAX), p1 = p0;
+    int a2 = 0;
+    if (lane < 9) {
+        const int oy = lane % 3 - 1, oz = lane / 3 - 1;
+        int yy = cy + oy, zz = cz + oz;
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        const int rb = nx * (yy + ny * zz);
+        const int e1 = min(1, brk - 1);
+        a2 = brk;
+        if (-1 <= e1) p0 = row_piece(start, rb, cx == 0 ? nx - 1 : cx - 1, e1 + 2, n);
+        if (brk < 2) p1 = row_piece(start, rb, cx + a2 >= nx ? cx + a2 - nx : cx + a2, 2 - a2, n);
+        n0 = p0.y - p0.x;
+        len = n0 + (p1.y - p1.x);
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kAll, incl, 31);
+    if (lane < 9) {
+        const int oy = lane % 3 - 1, oz = lane / 3 - 1;
+        const int f0 = incl - len;
+        const T offy = (T)oy * hy, offz = (T)oz * hz;
+        const int cb = 3 * (oy + 1) + 9 * (oz + 1);
+        sh.pc[2 * lane] = make_int4(p0.x, p0.z, p0.w, f0);
+        sh.po[2 * lane] = mk4(-hx, offy, offz, (T)0);
+        sh.code[2 * lane] = cb;
+        sh.pc[2 * lane + 1] = make_int4(p1.x, p1.z, p1.w, f0 + n0);
+        sh.po[2 * lane + 1] = mk4((T)a2 * hx, offy, offz, (T)0);
+        sh.code[2 * lane + 1] = cb + a2 + 1;
+    }
+    __syncwarp();
+    const int cap = b.cap;
+    for (int h0 = 0; h0 < m; h0 += kHomeChunk) {
+        const int mh = min(kHomeChunk, m - h0);
+        if (lane < mh) sh.home[lane] = xc[hs + h0 + lane];
+        __syncwarp();
+        int cnt = 0;                             // lane a: accepted count of cell atom a
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            bool ok = false;
+            int j = -1, o = 0;
+            T cxj = (T)0, cyj = (T)0, czj = (T)0;
+            if (t < total) {
+                int e = 0;                       // piece of t: last entry whose flat start is <= t
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int q = e + step;
+                    if (q < kRowPieces && sh.pc[q].w <= t) e = q;
+                }
+                const int4 pc = sh.pc[e];
+                const T4 po = sh.po[e];
+                const int p = pc.x + (t - pc.w);
+                const T4 xj = xc[p];
+                j = unpack_index(xj.w);
+                const int inc = (p >= pc.y ? 1 : 0) + (p >= pc.z ? 1 : 0);
+                o = sh.code[e] + inc;
+                cxj = xj.x + (po.x + (T)inc * hx);
+                cyj = xj.y + po.y;
+                czj = xj.z + po.z;
+                ok = (unsigned)(j - off) < (unsigned)n;
+                if (!ok) atomicOr(&st.err, NEFE_ERR_CELL);
+            }
+            for (int a = 0; a < mh; ++a) {
+                const T4 ha = sh.home[a];
+                const int ia = unpack_index(ha.w);
+                const T dx = cxj - ha.x, dy = cyj - ha.y, dz = czj - ha.z;
+                const T dd = dx * dx + dy * dy + dz * dz;
+                const bool cand = ok && !(j == ia && o == 13);
+                bool in = cand && dd < lo2;
+                const bool band = cand && !(dd < lo2) && dd <= hi2;
+                if (__any_sync(kAll, band)) {    // rare: decided by the exact FP64 criterion
+                    if (band) {
+                        double d[3];
+                        in = exact_pair_in(b, st.box, ia, j, __dmul_rn(S.rcs, S.rcs), d);
+                        in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
+                             fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
+                             fabs(d[2] - (double)dz) < 0.5 * st.h[2];
+                    }
+                }
+                const unsigned bal = __ballot_sync(kAll, in);
+                const int base = __shfl_sync(kAll, cnt, a);
+                const int pos = base + __popc(bal & ((1u << lane) - 1u));
+                if (in && pos < kMaxCap) sh.keys[a][pos] = (unsigned)j * 32u + (unsigned)o;
+                if (lane == a) cnt += __popc(bal);
+            }
+        }
+        __syncwarp();
+        // rank each cell atom's keys by atom index (one key per lane; the row padded to a
+        // multiple of 4 with the largest key and read 4 keys at a time)
+        for (int a = 0; a < mh; ++a) {
+            const int ca = __shfl_sync(kAll, cnt, a);
+            const int ia = unpack_index(sh.home[a].w);
+            const int have = ca < kMaxCap ? ca : kMaxCap;
+            const int have4 = (have + 3) & ~3;
+            if (have + lane < have4) sh.keys[a][have + lane] = 0xffffffffu;
+            __syncwarp();
+            const int mrow = ca < cap ? ca : cap;
+            int* out = b.nbr + (size_t)ia * cap;
+            const uint4* row4 = reinterpret_cast<const uint4*>(sh.keys[a]);
+            for (int k0 = 0; k0 < have; k0 += 32) {
+                const int kk = k0 + lane;
+                const unsigned key = kk < have ? sh.keys[a][kk] : 0xffffffffu;
+                int rk = 0;
+                for (int z = 0; z < have4; z += 4) {
+                    const uint4 v = row4[z >> 2];
+                    rk += (v.x < key ? 1 : 0) + (v.y < key ? 1 : 0) + (v.z < key ? 1 : 0) + (v.w < key ? 1 : 0);
+                }
+                if (kk < have && rk < mrow) out[rk] = (int)((key >> 5) | ((key & 31u) << kCodeShift));
+            }
+            if (lane == 0) {
+                b.cnt[ia] = ca;
+                if (ca > cap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
+            }
+        }
+        __syncwarp();                            // the home table and key rows are reused
+    }
+}
+
+// Each warp takes a contiguous range of the worklist cells: with a worklist, the cells of the
+// flagged systems in system order (rcbase[s] = first worklist cell of system s, rcbase[nsys] =
+// their number); without one (stateless calls, one system), every cell of system 0.
+template <typename T>
+__global__ void __launch_bounds__(kTile, 8) k_nlist_cell(Bufs b, int nsys) {
+    __shared__ CellListShared<T> shm[kTile / 32];
+    const int lane = threadIdx.x & 31;
+    CellListShared<T>& sh = shm[threadIdx.x >> 5];
+    const int nw = gridDim.x * (kTile / 32);
+    const int wid = blockIdx.x * (kTile / 32) + (int)(threadIdx.x >> 5);
+    int C;
+    if (b.rcbase) {
+        C = b.rcbase[nsys];
+    } else {
+        const DevState& s0 = b.st[0];
+        C = s0.ncell[0] * s0.ncell[1] * s0.ncell[2];
+    }
+    const int K = (C + nw - 1) / nw;
+    const int g0 = wid * K, g1 = min(C, g0 + K);
+    if (g0 >= g1) return;
+    int s = 0;
+    if (b.rcbase) {                              // largest s with rcbase[s] <= g0
+        int lo = 0, hi = nsys;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (b.rcbase[mid] <= g0) lo = mid; else hi = mid;
+        }
+        s = lo;
+    }
+    for (int g = g0; g < g1; ++g) {
+        if (b.rcbase) {
+            while (s + 1 < nsys && b.rcbase[s + 1] <= g) ++s;
+        }
+        nlist_cell<T>(b, s, g - (b.rcbase ? b.rcbase[s] : 0), sh, lane);
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Uhlenbeck-Ford fluid (the liquid's reference system, Sec. 2.1):
 //   u(r) = -p kT ln(1 - exp(-r^2/sigma^2)) - u(rc),  r < rc.
@@ -2140,7 +2389,14 @@ void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, i
                            cudaStream_t s, long* launches) {
     if (ntiles <= 0) return;
     launch_cells(b, precision, ntiles, nsys, force_all, s, launches);
-    const int L = (b.list_lanes == 16 || b.list_lanes == 32) ? b.list_lanes : 8;
+    const int L = (b.list_lanes == 8 || b.list_lanes == 16 || b.list_lanes == 32) ? b.list_lanes : 0;
+    if (L == 0) {
+        const int g = b.rtiles ? kRebuildBlocks : max(1, min(kRebuildBlocks, ntiles * 8));
+        if (precision == NEFE_FP64) k_nlist_cell<double><<<g, kTile, 0, s>>>(b, nsys);
+        else k_nlist_cell<float><<<g, kTile, 0, s>>>(b, nsys);
+        if (launches) *launches += 1;
+        return;
+    }
     const int g = rebuild_grid(b, ntiles * L);
     if (precision == NEFE_FP64) {
         if (L == 8) k_nlist<double, 8><<<g, kTile, 0, s>>>(b);

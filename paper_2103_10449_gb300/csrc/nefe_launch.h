@@ -43,6 +43,8 @@ struct Bufs {
     int tile_base;           // first tile of the launch (force passes run in L2-sized chunks)
     int* rtiles;             // rebuild worklist (tiles of flagged systems) or NULL
     int* rcount;             // its length
+    int* rcbase;             // [nsys + 1] first worklist cell of each system (cells of flagged
+                             // systems, in system order; the last entry is their number) or NULL
     double dt;
     const void* swc;         // SWc<float> or SWc<double> table
     DevPair* pairs;
@@ -50,7 +52,7 @@ struct Bufs {
     double* f_out;           // stateless: FP64 SoA forces
     double* e_atom;          // stateless: per-atom energy (may be NULL)
     int want_grad;           // pass A also sums dE/d(A, B, p, q, a, lambda3, gamma)
-    int list_lanes;          // lanes per atom of the list build (8, 16 or 32; 0: 8)
+    int list_lanes;          // list build: 0 one warp per cell; 8, 16 or 32 lanes per atom
     int* uf_nbr;             // [ntot][kUfCap] Uhlenbeck-Ford pair rows (NULL: no UF system)
     int* uf_cnt;             // [ntot] their lengths
     void* uf_F;              // [ntot] UF force and atom energy of the step (T4)

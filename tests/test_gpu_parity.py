@@ -225,10 +225,10 @@ def test_pass_b_lanes_close_to_oracle(N, gather_lanes):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_list_lanes_leave_the_run_bitwise_unchanged(N, precision):
-    """The list build's output is integer and ranked by atom index: its lane count cannot
-    change anything downstream."""
-    runs = [_fl_pair(precision, nsteps=150, list_lanes=ll) for ll in (8, 16, 32)]
+def test_list_forms_leave_the_run_bitwise_unchanged(N, precision):
+    """The list build's output is integer and ranked by atom index: its form (one warp per
+    cell, or 8, 16, 32 lanes per atom) cannot change anything downstream."""
+    runs = [_fl_pair(precision, nsteps=150, list_lanes=ll) for ll in (0, 8, 16, 32)]
     for r in runs[1:]:
         assert r[1]["W"] == runs[0][1]["W"] and np.array_equal(r[2], runs[0][2])
 
