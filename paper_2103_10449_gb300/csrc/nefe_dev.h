@@ -32,7 +32,9 @@ enum Acc {
     ACC_KT = ACC_VIR + 6,   // 6: sum m v_a v_b (eV)
     ACC_XI = ACC_KT + 6,    // 3: sum of thermostat normals of the current step
     ACC_DTH = ACC_XI + 3,   // 7: dE/d(A, B, p, q, a, lambda3, gamma) (stateless gradient call)
-    ACC_N = ACC_DTH + 7
+    ACC_XIN = ACC_DTH + 7,  // 3: sum of the next step's thermostat normals, drawn by an epilogue
+                            //    that already moved the atoms (becomes ACC_XI at the next step)
+    ACC_N = ACC_XIN + 3
 };
 
 enum Sched { SCHED_NONE = 0, SCHED_FL = 1, SCHED_RS = 2, SCHED_AS = 3 };
@@ -106,7 +108,8 @@ struct DevState {
     double thr2;                // squared displacement that triggers a rebuild
     double dHdl, H, V, P[6];    // last observation
     unsigned err;
-    int pad;
+    int rebuild_next;           // set by the epilogue that already moved the atoms for the next
+                                // step (systems without a barostat); becomes `rebuild` at that step
     long long trace_n;
     long long nbuild;           // list builds so far
     // FP32 copies of this step's constants (written with their FP64 sources)

@@ -157,8 +157,9 @@ int not_ready(nefe_ctx* c, const char* what) {
 double rc_of(const HostSys& h) { return h.prm.a * h.prm.sigma; }
 
 // Both force passes, chunk by chunk; with slot >= 0 (profiling capture) events bracket
-// every chunk's pass A and pass B.
-void enqueue_forces(nefe_ctx* c, int mode, int slot = -1) {
+// every chunk's pass A and pass B.  fuse: the scatter form's epilogue also runs the next
+// step's kick and drift for the systems without a barostat.
+void enqueue_forces(nefe_ctx* c, int mode, int slot = -1, int fuse = 0) {
     if (c->n_uf_tiles > 0) launch_uf(c->b, c->prec, c->n_uf_tiles, mode, c->stream, &c->launches);
     const int nch = (int)c->chunk_tile0.size();
     for (int k = 0; k < nch; ++k) {
@@ -169,17 +170,24 @@ void enqueue_forces(nefe_ctx* c, int mode, int slot = -1) {
         if (prof) cudaEventRecordWithFlags(c->ev0[e], c->stream, cudaEventRecordExternal);
         launch_edges(b, c->prec, c->lanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
         if (prof) cudaEventRecordWithFlags(c->ev1[e], c->stream, cudaEventRecordExternal);
-        launch_gather(b, c->prec, c->lanes == 0 ? 0 : c->glanes, c->chunk_ntile[k], mode, c->stream, &c->launches);
+        launch_gather(b, c->prec, c->lanes == 0 ? 0 : c->glanes, c->chunk_ntile[k], mode, c->stream, &c->launches,
+                      fuse);
         if (prof) cudaEventRecordWithFlags(c->ev2[e], c->stream, cudaEventRecordExternal);
     }
 }
 
-void enqueue_step(nefe_ctx* c, int slot = -1) {
-    launch_group(c->b, c->d_groups, c->ngroups, 1, c->stream, &c->launches);
-    launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches);
+// One MD step.  first / last: the step's place in a sequence enqueued together (a captured
+// graph, or the steps left over after the graph replays).  In the scatter form, every step but
+// the last hands the next step's kick and drift of the systems without a barostat to its own
+// epilogue (k_finish), so that the next step's k_kick_drift skips them; the last step of a
+// sequence does not, so between calls the state is at a full step as usual.
+void enqueue_step(nefe_ctx* c, int slot = -1, bool first = true, bool last = true) {
+    const bool fused = c->lanes == 0;            // k_finish is the epilogue
+    launch_group(c->b, c->d_groups, c->ngroups, 1, c->stream, &c->launches, fused && !first);
+    launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches, fused && !first);
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
     if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
-    enqueue_forces(c, FM_STEP, slot);
+    enqueue_forces(c, FM_STEP, slot, fused && !last);
 }
 
 void fill_results(const DevSys& S, const DevState& st, nefe_results* out) {
@@ -691,7 +699,8 @@ int nefe_run(nefe_ctx* c, long nsteps) {
         if (c->profiling && (rc = ensure_events(c))) return rc;
         NEFE_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         long before = c->launches;
-        for (int k = 0; k < kGraphSteps; ++k) enqueue_step(c, c->profiling ? k : -1);
+        for (int k = 0; k < kGraphSteps; ++k)
+            enqueue_step(c, c->profiling ? k : -1, k == 0, k == kGraphSteps - 1);
         c->launches = before;
         cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -702,7 +711,7 @@ int nefe_run(nefe_ctx* c, long nsteps) {
         NEFE_CU(cudaGraphLaunch(c->gexec, c->stream));
         c->launches += (long)kGraphSteps * launches_per_step(c);
     }
-    for (long r = 0; r < rem; ++r) enqueue_step(c);
+    for (long r = 0; r < rem; ++r) enqueue_step(c, -1, r == 0, r == rem - 1);
     NEFE_CU(cudaGetLastError());
     return NEFE_OK;
 }

@@ -182,6 +182,21 @@ __device__ __forceinline__ void offset_table(typename V4<T>::t* tab, T hx, T hy,
     __syncthreads();
 }
 
+// The same 27 offset vectors as three component rows of 32 (row k, entry c at tab[32 k + c]):
+// a warp whose lanes index different entries reads each row without bank conflicts (a table
+// of 16-byte vectors indexed at random serialises).  Every thread of the block must call it.
+template <typename T>
+__device__ __forceinline__ void offset_rows(T* tab, T hx, T hy, T hz) {
+    if (threadIdx.x < 27) {
+        const int c = threadIdx.x;
+        const int ox = c % 3 - 1, oy = (c / 3) % 3 - 1, oz = c / 9 - 1;
+        tab[c] = ox == 0 ? (T)0 : (ox < 0 ? -hx : hx);
+        tab[32 + c] = oy == 0 ? (T)0 : (oy < 0 ? -hy : hy);
+        tab[64 + c] = oz == 0 ? (T)0 : (oz < 0 ? -hz : hz);
+    }
+    __syncthreads();
+}
+
 // Cell grid for a box: per axis floor(L/rcs), reduced while L/n < rcs (1 + 1e-9); then the
 // largest axis is reduced until the product fits the capacity (wider cells stay valid).
 __device__ __forceinline__ bool grid_for(const double box[3], double rcs, int cap, int n3[3]) {
@@ -1216,27 +1231,73 @@ __device__ __forceinline__ void comp_add(T& hi, T& lo, T d) {
     }
 }
 
+// Drift of atom i by its half-kicked velocity vk (move), its mirror, the displacement test (sets
+// *flag) and the thermostat noise of step kstep (stored, and returned in z).  dh, dl: the atom's
+// displacement, updated in place.  Shared by k_kick_drift and by the epilogue that moves the
+// atoms for the next step (systems without a barostat), so both do the same operations.
 template <typename T>
-__global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
+__device__ __forceinline__ void drift_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
+                                           const T (&vk)[3], bool move, T (&dh)[3], T (&dl)[3],
+                                           int flag_set, int* flag, unsigned long long kstep, T (&z)[3]) {
+    using T4 = typename V4<T>::t;
+    const size_t N = b.ntot;
+    T* DH = reinterpret_cast<T*>(b.dhi);
+    T* DL = reinterpret_cast<T*>(b.dlo);
+    const T4 xa = reinterpret_cast<const T4*>(b.xa)[i];
+    const T xav[3] = {xa.x, xa.y, xa.z};
+    const bool scaled = st.scaled != 0, hmoved = st.hmoved != 0;
+    int4 q = make_int4(0, 0, 0, 0);
+    if (scaled || hmoved) q = b.q[i];
+    const int qa[3] = {q.x, q.y, q.z};
+    if (move) {
+        const T dt = pick<T>(b.dt, S.dt_f);
+        for (int k = 0; k < 3; ++k) {
+            T d = dt * pick<T>(st.phi[k], st.phi_f[k]) * vk[k];
+            if (scaled) {   // (s - 1) x with x = xa + q hb + displacement
+                const T xk = xav[k] + (T)qa[k] * pick<T>(st.hb[k], st.hb_f[k]) + dh[k];
+                d += pick<T>(st.s[k] - 1.0, st.sm1_f[k]) * xk;
+            }
+            comp_add<T>(dh[k], dl[k], d);
+            DH[k * N + i] = dh[k];
+            if constexpr (sizeof(T) == 4) DL[k * N + i] = dl[k];
+        }
+    }
+    T m[3];
+    for (int k = 0; k < 3; ++k) {
+        m[k] = xav[k] + (dh[k] + dl[k]);
+        if (hmoved) m[k] -= (T)qa[k] * (pick<T>(st.h[k], st.h_f[k]) - pick<T>(st.hb[k], st.hb_f[k]));
+    }
+    reinterpret_cast<T4*>(b.xs)[i] = mk4(m[0], m[1], m[2], (T)0);
+    T dd2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        const T dd = hmoved ? m[k] - xav[k] * pick<T>(st.h[k] / st.hb[k], st.rho_f[k]) : dh[k] + dl[k];
+        dd2 += dd * dd;
+    }
+    if (dd2 > pick<T>(st.thr2, st.thr2_f) && !flag_set) atomicOr(flag, 1);
+    z[0] = z[1] = z[2] = (T)0;
+    if (S.thermo) {
+        Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)kstep, (uint64_t)(i - S.off), z);
+        reinterpret_cast<T4*>(b.xi)[i] = mk4(z[0], z[1], z[2], (T)0);
+    }
+}
+
+// skip: systems without a barostat were already kicked and moved by the previous step's
+// epilogue (k_finish with fuse), so their tiles return at once.
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode, int skip) {
     using T4 = typename V4<T>::t;
     const TileAtom ta = tile_of(b, blockIdx.x);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
-    DevState& gst = st;
+    if (skip && S.baro == BARO_NONE) return;     // uniform over the block (one system per tile)
     T xs_sum[3] = {(T)0, (T)0, (T)0};
     if ((int)threadIdx.x < ta.count) {
         const int i = ta.first + threadIdx.x;
         const size_t N = b.ntot;
         T* V = reinterpret_cast<T*>(b.v);
-        T* DH = reinterpret_cast<T*>(b.dhi);
-        T* DL = reinterpret_cast<T*>(b.dlo);
-        const T4 xa = reinterpret_cast<const T4*>(b.xa)[i];
-        const T xav[3] = {xa.x, xa.y, xa.z};
-        const bool scaled = st.scaled != 0, hmoved = st.hmoved != 0;
-        int4 q = make_int4(0, 0, 0, 0);
-        if (scaled || hmoved) q = b.q[i];
-        const int qa[3] = {q.x, q.y, q.z};
-        T dh[3], dl[3];
+        const T* DH = reinterpret_cast<const T*>(b.dhi);
+        const T* DL = reinterpret_cast<const T*>(b.dlo);
+        T dh[3], dl[3], vk[3] = {(T)0, (T)0, (T)0};
         for (int k = 0; k < 3; ++k) {
             dh[k] = DH[k * N + i];
             if constexpr (sizeof(T) == 4) dl[k] = DL[k * N + i]; else dl[k] = (T)0;
@@ -1244,40 +1305,16 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode) {
         if (mode == 1) {
             const T4 F = reinterpret_cast<const T4*>(b.F)[i];
             const T fv[3] = {F.x, F.y, F.z};
-            const T ck = pick<T>(S.ckick, S.ckick_f), dt = pick<T>(b.dt, S.dt_f);
+            const T ck = pick<T>(S.ckick, S.ckick_f);
             for (int k = 0; k < 3; ++k) {
-                const T vk = V[k * N + i] + ck * fv[k];
-                V[k * N + i] = vk;
-                T d = dt * pick<T>(st.phi[k], st.phi_f[k]) * vk;
-                if (scaled) {   // (s - 1) x with x = xa + q hb + displacement
-                    const T xk = xav[k] + (T)qa[k] * pick<T>(st.hb[k], st.hb_f[k]) + dh[k];
-                    d += pick<T>(st.s[k] - 1.0, st.sm1_f[k]) * xk;
-                }
-                comp_add<T>(dh[k], dl[k], d);
-                DH[k * N + i] = dh[k];
-                if constexpr (sizeof(T) == 4) DL[k * N + i] = dl[k];
+                vk[k] = V[k * N + i] + ck * fv[k];
+                V[k * N + i] = vk[k];
             }
         }
-        T m[3];
-        for (int k = 0; k < 3; ++k) {
-            m[k] = xav[k] + (dh[k] + dl[k]);
-            if (hmoved) m[k] -= (T)qa[k] * (pick<T>(st.h[k], st.h_f[k]) - pick<T>(st.hb[k], st.hb_f[k]));
-        }
-        reinterpret_cast<T4*>(b.xs)[i] = mk4(m[0], m[1], m[2], (T)0);
-        T dd2 = 0;
-        for (int k = 0; k < 3; ++k) {
-            const T dd = hmoved ? m[k] - xav[k] * pick<T>(st.h[k] / st.hb[k], st.rho_f[k]) : dh[k] + dl[k];
-            dd2 += dd * dd;
-        }
-        if (dd2 > pick<T>(st.thr2, st.thr2_f) && !st.rebuild) atomicOr(&gst.rebuild, 1);
-        if (S.thermo) {
-            T z[3];
-            Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)st.k, (uint64_t)(i - S.off), z);
-            reinterpret_cast<T4*>(b.xi)[i] = mk4(z[0], z[1], z[2], (T)0);
-            xs_sum[0] = z[0]; xs_sum[1] = z[1]; xs_sum[2] = z[2];
-        }
+        drift_atom<T>(b, S, st, i, vk, mode == 1, dh, dl, st.rebuild, &st.rebuild, (unsigned long long)st.k,
+                      xs_sum);
     }
-    block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &gst.err);
+    block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &st.err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1533,6 +1570,10 @@ constexpr int kEdges1Threads = 64;
 // a streaming epilogue (k_finish) reads and clears each atom's accumulator.  A term is
 // rounded to 2^-22 eV/A; one above kLegLimit eV/A (whose sum over the terms an atom can
 // receive could overflow int32) is dropped and flags the system.
+// The x and y terms travel in one 64-bit reduction as y 2^32 + x (two's complement, modulo
+// 2^64): integer addition is linear, so the 64-bit word accumulates Y 2^32 + X exactly, X and Y
+// being the int32 sums.  Its low word is X; its high word is Y - 1 when X < 0 (the borrow), which
+// the reader undoes (force_of_acc).  Two reductions per force instead of three.
 constexpr float kLegScale = 2097152.0f;          // 2^21
 constexpr float kLegLimit = 48.0f;
 __device__ __forceinline__ void red_force(int* acc4, float x, float y, float z, unsigned* err) {
@@ -1540,9 +1581,15 @@ __device__ __forceinline__ void red_force(int* acc4, float x, float y, float z, 
         atomicOr(err, NEFE_ERR_NAN);
         return;
     }
-    atomicAdd(acc4 + 0, __float2int_rn(x * kLegScale));
-    atomicAdd(acc4 + 1, __float2int_rn(y * kLegScale));
+    const long long px = __float2int_rn(x * kLegScale), py = __float2int_rn(y * kLegScale);
+    const unsigned long long xy = ((unsigned long long)py << 32) + (unsigned long long)px;
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc4), xy);
     atomicAdd(acc4 + 2, __float2int_rn(z * kLegScale));
+}
+
+// The int32 sums (X, Y, Z) of an accumulator written by red_force.
+__device__ __forceinline__ int3 force_of_acc(int4 q) {
+    return make_int3(q.x, q.y + (q.x < 0 ? 1 : 0), q.z);
 }
 
 constexpr int kEdges1K1 = kShell1Shared;
@@ -1556,7 +1603,7 @@ constexpr int kEdges1K1 = kShell1Shared;
 // pos(j) returns atom j's mirror position (from global memory or a shared copy).
 template <typename T, bool SCATTER, int NT, typename PosFn>
 __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevState& st,
-                                            const typename V4<T>::t* soff, int i, int t,
+                                            const T* soff, int i, int t,
                                             typename V4<T>::t (*sh_u)[NT], T (*sh_r)[NT], int (*sh_j)[NT],
                                             PosFn pos, T (&red8)[8]) {
     using T4 = typename V4<T>::t;
@@ -1594,8 +1641,9 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (base + u >= ci) continue;
-            const T4 oh = soff[(unsigned)e[u] >> kCodeShift];
-            const T dx = (xj[u].x - xi.x) + oh.x, dy = (xj[u].y - xi.y) + oh.y, dz = (xj[u].z - xi.z) + oh.z;
+            const unsigned c = (unsigned)e[u] >> kCodeShift;
+            const T dx = (xj[u].x - xi.x) + soff[c], dy = (xj[u].y - xi.y) + soff[32 + c],
+                    dz = (xj[u].z - xi.z) + soff[64 + c];
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < P.act2) {
                 if (m < capm) {
@@ -1698,7 +1746,7 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
 template <typename T, bool SCATTER>
 __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4<T>::t (*sh_u)[kEdges1Threads],
                                             T (*sh_r)[kEdges1Threads], int (*sh_j)[kEdges1Threads],
-                                            typename V4<T>::t* soff) {
+                                            T* soff) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
     // 20 bytes per shell entry and thread (occupancy is bound by this table):
@@ -1709,7 +1757,7 @@ __device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4
     DevState& st = b.st[ta.sys];
     if (S.pot != POT_SW) return;                 // uniform over the block
     const SWc<T> P = reinterpret_cast<const SWc<T>*>(b.swc)[S.prm];
-    offset_table<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
+    offset_rows<T>(soff, pick<T>(st.h[0], st.h_f[0]), pick<T>(st.h[1], st.h_f[1]), pick<T>(st.h[2], st.h_f[2]));
     const int t = threadIdx.x;
     const int ia = part * NT + t;
     T red8[8] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};   // scatter form: energy, -, virial
@@ -1727,7 +1775,7 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     __shared__ T4 sh_u[kEdges1K1][kEdges1Threads];   // (d, r^2) after compaction, then (u, g)
     __shared__ T sh_r[kEdges1K1][kEdges1Threads];    // r
     __shared__ int sh_j[SCATTER ? kEdges1K1 : 1][kEdges1Threads];   // shell atom indices (scatter form)
-    __shared__ T4 soff[27];
+    __shared__ T soff[3 * 32];
     edges1_item<T, SCATTER>(b, blockIdx.x, sh_u, sh_r, sh_j, soff);
 }
 
@@ -1741,7 +1789,8 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
 template <typename T, int MODE>
 __device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
                                             const T (&f)[3], T e_i, bool write_e, const T (&pd)[3],
-                                            const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14]);
+                                            const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14],
+                                            bool keep, T (&vo)[3], T (&Fo)[3]);
 template <typename T>
 __device__ __forceinline__ void noise_mean(const Bufs& b, const DevSys& S, int sys, T* s_xm);
 template <typename T>
@@ -1870,7 +1919,8 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                 red[2] = wa.x; red[3] = wa.y; red[4] = wa.z; red[5] = wa.w; red[6] = wb.x; red[7] = wb.y;
             }
         }
-        if (lane == 0) finish_atom<T, MODE>(b, S, st, i, f, e_i, true, pd, pv, pz, s_xm, red);
+        T vo[3], Fo[3];
+        if (lane == 0) finish_atom<T, MODE>(b, S, st, i, f, e_i, true, pd, pv, pz, s_xm, red, false, vo, Fo);
     }
     block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &gst.err);
 }
@@ -1879,10 +1929,13 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
 // Einstein springs / UF force, lambda mixing, Langevin force with the per-system mean of this
 // step's noise removed, second half kick, total force for the next step and the kinetic sums.
 // pd: spring offset x - r0; pv: velocity; pz: noise of the step; s_xm: the per-system noise mean.
+// keep: the velocity and total force are returned in vo, Fo instead of being stored (the caller
+// goes on to the next step's kick and drift).
 template <typename T, int MODE>
 __device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
                                             const T (&f)[3], T e_i, bool write_e, const T (&pd)[3],
-                                            const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14]) {
+                                            const T (&pv)[3], const T (&pz)[3], const T* s_xm, T (&red)[14],
+                                            bool keep, T (&vo)[3], T (&Fo)[3]) {
     using T4 = typename V4<T>::t;
     const size_t N = b.ntot;
             if (MODE == FM_FORCES) {
@@ -1920,9 +1973,13 @@ __device__ __forceinline__ void finish_atom(const Bufs& b, const DevSys& S, cons
                 }
                 if (MODE == FM_STEP) {
                     const T ck = pick<T>(S.ckick, S.ckick_f);
-                    for (int k = 0; k < 3; ++k) { v[k] += ck * F[k]; V[k * N + i] = v[k]; }
+                    for (int k = 0; k < 3; ++k) {
+                        v[k] += ck * F[k];
+                        if (!keep) V[k * N + i] = v[k];
+                    }
                 }
-                reinterpret_cast<T4*>(b.F)[i] = mk4(F[0], F[1], F[2], (T)0);
+                for (int k = 0; k < 3; ++k) { vo[k] = v[k]; Fo[k] = F[k]; }
+                if (!keep) reinterpret_cast<T4*>(b.F)[i] = mk4(F[0], F[1], F[2], (T)0);
                 const T me = pick<T>(S.mass_e, S.mass_f);
                 red[0] += u_int;
                 red[1] = u_ref;
@@ -1971,8 +2028,17 @@ __device__ __forceinline__ void noise_mean(const Bufs& b, const DevSys& S, int s
 // Force pass B of the scatter form: one thread per atom reads and clears the atom's force
 // accumulator (the pair, own-triplet and leg forces pass A added) and runs the epilogue.  The
 // SW energy and virial were summed by pass A.
+// fuse (FM_STEP, systems without a barostat): the epilogue goes straight on to the next step's
+// first half kick, drift, mirror, displacement test and thermostat noise -- the work of
+// k_kick_drift, which then skips these systems.  Nothing between the two reads or changes what
+// that work uses (no barostat: the box, drift factors and rebuild threshold stay as they are),
+// and the operations are the same ones, so the trajectory is bit for bit that of the unfused
+// sequence.  The force of the step is not stored (the next half kick consumed it); the noise
+// sums go to ACC_XIN and the rebuild flag to rebuild_next, which the next k_group moves into
+// place.  The last step of every launch sequence runs unfused, so the state between calls is
+// the usual one (positions and velocities at a full step).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
+__global__ void __launch_bounds__(kTile) k_finish(Bufs b, int fuse) {
     using T4 = typename V4<T>::t;
     const int tile = blockIdx.x + b.tile_base;
     __shared__ __align__(16) StagedSys sh;
@@ -1989,9 +2055,11 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
     DevState& gst = b.st[ta.sys];
     if (MODE != FM_FORCES) noise_mean_staged<T>(S, s_xi, s_xm);
     __syncthreads();
+    const bool fz = MODE == FM_STEP && fuse && S.baro == BARO_NONE;   // uniform over the block
     T red[14];
 #pragma unroll
     for (int k = 0; k < 14; ++k) red[k] = (T)0;
+    T zn[3] = {(T)0, (T)0, (T)0};
     if ((int)threadIdx.x < ta.count) {
         const int i = ta.first + threadIdx.x;
         const size_t N = b.ntot;
@@ -2004,10 +2072,10 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
         T4 d0 = mk4((T)0, (T)0, (T)0, (T)0), z = d0;
         T dh[3] = {(T)0, (T)0, (T)0}, dl[3] = {(T)0, (T)0, (T)0}, pv[3] = {(T)0, (T)0, (T)0};
         if (sw) q = *a4;
-        if (springs) {
+        if (springs || fz) {
             const T* DH = reinterpret_cast<const T*>(b.dhi);
             const T* DL = reinterpret_cast<const T*>(b.dlo);
-            d0 = reinterpret_cast<const T4*>(b.sd0)[i];
+            if (springs) d0 = reinterpret_cast<const T4*>(b.sd0)[i];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 dh[k] = DH[k * N + i];
@@ -2023,10 +2091,24 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b) {
         const T pd[3] = {d0.x + dh[0] + dl[0], d0.y + dh[1] + dl[1], d0.z + dh[2] + dl[2]};
         const T pz[3] = {z.x, z.y, z.z};
         const T inv = (T)(1.0 / (double)kLegScale);
-        const T f[3] = {(T)q.x * inv, (T)q.y * inv, (T)q.z * inv};
-        finish_atom<T, MODE>(b, S, st, i, f, (T)0, false, pd, pv, pz, s_xm, red);
+        const int3 fq = force_of_acc(q);
+        const T f[3] = {(T)fq.x * inv, (T)fq.y * inv, (T)fq.z * inv};
+        T vo[3], Fo[3];
+        finish_atom<T, MODE>(b, S, st, i, f, (T)0, false, pd, pv, pz, s_xm, red, fz, vo, Fo);
+        if (fz) {
+            // the next step's first half kick (the force of this step, Langevin term included)
+            T* V = reinterpret_cast<T*>(b.v);
+            const T ck = pick<T>(S.ckick, S.ckick_f);
+            T vk[3];
+            for (int k = 0; k < 3; ++k) {
+                vk[k] = vo[k] + ck * Fo[k];
+                V[k * N + i] = vk[k];
+            }
+            drift_atom<T>(b, S, st, i, vk, true, dh, dl, 0, &gst.rebuild_next, (unsigned long long)st.k + 1ULL, zn);
+        }
     }
     block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &gst.err);
+    if (fz) block_sum_to_acc<T, 3>(zn, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XIN, &gst.err);
 }
 
 // FP64 positions and velocities for output, and replacement from FP64 input.
@@ -2171,7 +2253,11 @@ __device__ void prepare_step(const DevSys& S, DevState& st, double dt) {
     st.thr2_f = (float)st.thr2;
 }
 
-__global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups, int mode) {
+// carry (mode 1): the previous step's epilogue already kicked and moved the systems without a
+// barostat and drew their noise for this step (k_finish with fuse): their next-step noise sums
+// (ACC_XIN) become this step's (ACC_XI) and rebuild_next becomes rebuild, instead of both being
+// cleared.
+__global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups, int mode, int carry) {
     const DevGroup gr = groups[blockIdx.x];
     const int members[2] = {gr.a, gr.b};
     const int nm = gr.b >= 0 ? 2 : 1;
@@ -2293,7 +2379,8 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
             for (int mi = 0; mi < nm; ++mi) {
                 DevState& st = sh[mi].st;
                 prepare_step(sh[mi].S, st, b.dt);
-                st.rebuild = 0;
+                st.rebuild = (carry && sh[mi].S.baro == BARO_NONE) ? st.rebuild_next : 0;
+                st.rebuild_next = 0;
                 st.k += 1;
             }
         }
@@ -2315,7 +2402,15 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
     if (mode != 2) {
         for (int mi = 0; mi < nm; ++mi) {
             long long* acc = b.acc + (size_t)members[mi] * ACC_N * kSlots;
-            for (int t = threadIdx.x; t < ACC_N * kSlots; t += blockDim.x) acc[t] = 0;
+            const bool moved = mode == 1 && carry && sh[mi].S.baro == BARO_NONE;
+            for (int t = threadIdx.x; t < ACC_N * kSlots; t += blockDim.x) {
+                const int a = t / kSlots;
+                long long v = 0;
+                if (moved && a >= ACC_XI && a < ACC_XI + 3) v = acc[t + (ACC_XIN - ACC_XI) * kSlots];
+                if (a < ACC_XIN) acc[t] = v;
+            }
+            __syncthreads();   // ACC_XIN is read above before it is cleared
+            for (int t = threadIdx.x; t < 3 * kSlots; t += blockDim.x) acc[ACC_XIN * kSlots + t] = 0;
         }
     }
 }
@@ -2452,10 +2547,11 @@ void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t 
     if (launches) *launches += 1;
 }
 
-void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {
+void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches,
+                       int skip) {
     if (ntiles <= 0) return;
-    if (precision == NEFE_FP64) k_kick_drift<double><<<ntiles, kTile, 0, s>>>(b, mode);
-    else k_kick_drift<float><<<ntiles, kTile, 0, s>>>(b, mode);
+    if (precision == NEFE_FP64) k_kick_drift<double><<<ntiles, kTile, 0, s>>>(b, mode, skip);
+    else k_kick_drift<float><<<ntiles, kTile, 0, s>>>(b, mode, skip);
     if (launches) *launches += 1;
 }
 
@@ -2501,9 +2597,9 @@ void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode,
 }
 
 template <typename T, int MODE>
-static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s) {
+static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s, int fuse) {
     switch (lanes) {
-        case 0: k_finish<T, MODE><<<ntiles, kTile, 0, s>>>(b); break;
+        case 0: k_finish<T, MODE><<<ntiles, kTile, 0, s>>>(b, fuse); break;
         case 1: k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b); break;
         case 2: k_gather<T, MODE, 2><<<ntiles * 2, kTile, 0, s>>>(b); break;
         case 8: k_gather<T, MODE, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
@@ -2512,16 +2608,16 @@ static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s
 }
 
 void launch_gather(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
-                   long* launches) {
+                   long* launches, int fuse) {
     if (ntiles <= 0) return;
     if (precision == NEFE_FP64) {
-        if (mode == FM_FORCES) gather_dispatch<double, FM_FORCES>(b, lanes, ntiles, s);
-        else if (mode == FM_SETUP) gather_dispatch<double, FM_SETUP>(b, lanes, ntiles, s);
-        else gather_dispatch<double, FM_STEP>(b, lanes, ntiles, s);
+        if (mode == FM_FORCES) gather_dispatch<double, FM_FORCES>(b, lanes, ntiles, s, 0);
+        else if (mode == FM_SETUP) gather_dispatch<double, FM_SETUP>(b, lanes, ntiles, s, 0);
+        else gather_dispatch<double, FM_STEP>(b, lanes, ntiles, s, fuse);
     } else {
-        if (mode == FM_FORCES) gather_dispatch<float, FM_FORCES>(b, lanes, ntiles, s);
-        else if (mode == FM_SETUP) gather_dispatch<float, FM_SETUP>(b, lanes, ntiles, s);
-        else gather_dispatch<float, FM_STEP>(b, lanes, ntiles, s);
+        if (mode == FM_FORCES) gather_dispatch<float, FM_FORCES>(b, lanes, ntiles, s, 0);
+        else if (mode == FM_SETUP) gather_dispatch<float, FM_SETUP>(b, lanes, ntiles, s, 0);
+        else gather_dispatch<float, FM_STEP>(b, lanes, ntiles, s, fuse);
     }
     if (launches) *launches += 1;
 }
@@ -2539,9 +2635,9 @@ void launch_inject(const Bufs& b, int precision, int ntiles, const double* x, co
 }
 
 void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,
-                  long* launches) {
+                  long* launches, int carry) {
     if (ngroups <= 0) return;
-    k_group<<<ngroups, kTile, 0, s>>>(b, groups, mode);
+    k_group<<<ngroups, kTile, 0, s>>>(b, groups, mode, carry);
     if (launches) *launches += 1;
 }
 

@@ -72,9 +72,10 @@ void launch_decode_grad(const long long* acc, double* out8, cudaStream_t s);
 // Rebuild sequence (only systems whose rebuild flag is set, or all when force_all).
 void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
                            cudaStream_t s, long* launches);
-// Half kick + drift + mirror + displacement check + noise sums (mode 0: no kick/drift).
+// Half kick + drift + mirror + displacement check + noise sums (mode 0: no kick/drift).  skip:
+// the systems without a barostat were moved by the previous step's fused epilogue.
 void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s,
-                       long* launches);
+                       long* launches, int skip = 0);
 // Uhlenbeck-Ford pair rows of the UF systems (after the cell fill; flagged systems only when a
 // rebuild worklist is set).
 void launch_uf_list(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches);
@@ -85,15 +86,18 @@ void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t 
 void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
                   long* launches);
 // Force pass B (gather leg forces; springs, Langevin and second half kick in FM_SETUP/FM_STEP).
+// fuse (scatter form, FM_STEP): systems without a barostat go on to the next step's kick, drift
+// and noise in the same kernel.
 void launch_gather(const Bufs& b, int precision, int lanes, int ntiles, int mode, cudaStream_t s,
-                   long* launches);
+                   long* launches, int fuse = 0);
 // FP64 positions (anchor + displacement) and FP64 velocities into SoA staging buffers.
 void launch_materialize(const Bufs& b, int precision, int ntiles, double* x, double* v, cudaStream_t s);
 // Replace positions (anchor, zero displacement) and/or velocities from FP64 SoA buffers.
 void launch_inject(const Bufs& b, int precision, int ntiles, const double* x, const double* v, cudaStream_t s);
-// Per-group scalar update. mode 0 INIT, 1 STEP, 2 OBSERVE.
+// Per-group scalar update. mode 0 INIT, 1 STEP, 2 OBSERVE.  carry (STEP): the previous epilogue
+// was fused (its next-step noise sums and rebuild flag are moved into place).
 void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,
-                  long* launches);
+                  long* launches, int carry = 0);
 // Mirror only (stateless force entry): q and xs from x with the list-build formula.
 void launch_mirror(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches);
 // Thermostat noise as FP64 (n,3).

@@ -241,6 +241,43 @@ def test_run_is_bitwise_deterministic(N, lanes):
     assert a[1]["W"] == b[1]["W"] and np.array_equal(a[2], b[2])
 
 
+def test_fused_epilogue_leaves_the_trajectory_bitwise_unchanged(N):
+    """In the scatter form, every step of a sequence but the last runs the next step's kick,
+    drift and noise inside its epilogue for the systems without a barostat.  101 steps in one
+    call (three 32-step graphs with fused epilogues, then five steps) must equal, bit for bit,
+    101 calls of one unfused step each -- for an NVT switching system (fused), an NPT system
+    (never fused) and list rebuilds along the way."""
+    from paper_2103_10449_gb300 import nefe
+    x0, box = I.diamond(3, 3, 3)
+    v0 = I.gaussian_velocities(len(x0), _sv(1000.0), 61)
+
+    def make():
+        ctx = nefe.Context(precision=nefe.NEFE_FP32, skin=SKIN, nbr_cap=CAP)
+        a = ctx.add_system(x0, box, v=v0, r0=x0)
+        ctx.set_thermostat(a, 1000.0, 0.1, 62)
+        ctx.set_schedule(a, nefe.NEFE_SCHED_FL, nsteps=400, k_E=5.0)
+        b = ctx.add_system(x0, box, v=v0)
+        ctx.set_thermostat(b, 1000.0, 0.1, 63)
+        ctx.set_barostat(b, nefe.NEFE_BARO_ISO, 1.0, 1.0)
+        ctx.set_tuning(0)
+        return ctx
+    one, many = make(), make()
+    one.run(101)
+    for _ in range(101):
+        many.run(1)
+    for s in range(2):
+        ra, rb = one.results(s), many.results(s)
+        assert ra["step"] == rb["step"] == 101 and ra["error"] == rb["error"] == 0
+        assert ra["W"] == rb["W"] and ra["U"] == rb["U"] and ra["T"] == rb["T"]
+        xa, va, ba = one.get_state(s)
+        xb, vb, bb = many.get_state(s)
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ba, bb)
+    builds = one.list_stats(0)[2]
+    one.close()
+    many.close()
+    assert builds > 1
+
+
 @pytest.mark.parametrize("lanes", [1, 0])
 def test_thread_per_atom_pass_a_with_spilled_shells(N, lanes):
     """A random liquid has in-cutoff shells beyond the 8 entries the one-thread-per-atom pass A
