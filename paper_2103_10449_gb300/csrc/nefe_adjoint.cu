@@ -26,6 +26,7 @@
 #include "nefe_dev.h"
 #include "nefe_host.h"
 #include "nefe_launch.h"
+#include "nefe_nvtx.h"
 
 namespace nefe {
 namespace ad {
@@ -657,6 +658,7 @@ extern "C" {
 int nefe_sw_dual(const double* x, const double* w, int n, const double box[3], double rcs, const int* nbr,
                  const int* cnt, int cap, const nefe_sw_params* prm, const double* dtheta, double* f,
                  double* fd, double* out16, void* stream) {
+    NvtxRange nvtx_("nefe_sw_dual");
     if (n < 0 || !box || cap < 1 || cap > kMaxCap || !valid_params(prm) || !out16 ||
         (n > 0 && (!x || !nbr || !cnt || !f || !fd)))
         return fail(NEFE_EINVAL, "nefe_sw_dual: bad argument");
@@ -754,6 +756,7 @@ int nefe_adjoint_destroy(nefe_adj* A) {
 }
 
 int nefe_adjoint_forward(nefe_adj* A, long nsteps, double* W) {
+    NvtxRange nvtx_("nefe_adjoint_forward");
     if (!A || nsteps < 1) return fail(NEFE_EINVAL, "nefe_adjoint_forward: bad argument");
     NEFE_CU(cudaSetDevice(A->device));
     int rc = prepare_schedule(A, nsteps);
@@ -775,6 +778,7 @@ int nefe_adjoint_forward(nefe_adj* A, long nsteps, double* W) {
 }
 
 int nefe_adjoint_backward(nefe_adj* A, double dW_dtheta[7], double* dW_dx0, double* dW_dv0) {
+    NvtxRange nvtx_("nefe_adjoint_backward");
     if (!A || !dW_dtheta) return fail(NEFE_EINVAL, "nefe_adjoint_backward: bad argument");
     if (A->nsteps < 1) return fail(NEFE_ESTATE, "nefe_adjoint_backward: run nefe_adjoint_forward first");
     NEFE_CU(cudaSetDevice(A->device));
@@ -837,6 +841,7 @@ int nefe_adjoint_backward(nefe_adj* A, double dW_dtheta[7], double* dW_dx0, doub
 
 int nefe_adjoint_tangent(nefe_adj* A, long nsteps, const double dtheta[7], const double* dx0,
                          const double* dv0, double* W, double* dW) {
+    NvtxRange nvtx_("nefe_adjoint_tangent");
     if (!A || nsteps < 1 || !dtheta) return fail(NEFE_EINVAL, "nefe_adjoint_tangent: bad argument");
     NEFE_CU(cudaSetDevice(A->device));
     const size_t b3 = sizeof(double) * 3 * (size_t)A->n;

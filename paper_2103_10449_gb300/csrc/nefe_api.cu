@@ -8,6 +8,7 @@
 #include "nefe_dev.h"
 #include "nefe_host.h"
 #include "nefe_launch.h"
+#include "nefe_nvtx.h"
 
 namespace nefe {
 
@@ -119,6 +120,7 @@ int nefe_sw_params_silicon(nefe_sw_params* out) {
 
 int nefe_cell_bin(const double* x, int n, const double box[3], double rcs, int ncell3[3],
                   int* cell_of, int* cell_start, int* perm, int ncell_cap, void* stream) {
+    NvtxRange nvtx_("nefe_cell_bin");
     if (n < 0 || !box || !ncell3 || (n > 0 && (!x || !cell_of || !perm)) || !cell_start)
         return fail(NEFE_EINVAL, "nefe_cell_bin: bad argument");
     if (n >= (1 << kCodeShift)) return fail(NEFE_EINVAL, "nefe_cell_bin: n above 2^27");
@@ -146,6 +148,7 @@ int nefe_cell_bin(const double* x, int n, const double box[3], double rcs, int n
 
 int nefe_neighbor_build(const double* x, int n, const double box[3], double rcs, int cap,
                         int* nbr, int* cnt, int* overflow, void* stream) {
+    NvtxRange nvtx_("nefe_neighbor_build");
     if (n < 0 || !box || cap < 1 || cap > kMaxCap || (n > 0 && (!x || !nbr || !cnt)))
         return fail(NEFE_EINVAL, "nefe_neighbor_build: bad argument");
     if (n >= (1 << kCodeShift)) return fail(NEFE_EINVAL, "nefe_neighbor_build: n above 2^27");
@@ -177,6 +180,7 @@ int nefe_neighbor_build(const double* x, int n, const double box[3], double rcs,
 int nefe_sw_forces(const double* x, int n, const double box[3], double rcs, const int* nbr,
                    const int* cnt, int cap, const nefe_sw_params* prm, int precision, double* f,
                    double* e_atom, double* energy_virial, int* shell_overflow, void* stream) {
+    NvtxRange nvtx_("nefe_sw_forces");
     if (n < 0 || !box || cap < 1 || cap > kMaxCap || !valid_params(prm) ||
         (precision != NEFE_FP32 && precision != NEFE_FP64) || (n > 0 && (!x || !nbr || !cnt || !f)))
         return fail(NEFE_EINVAL, "nefe_sw_forces: bad argument");
@@ -230,6 +234,7 @@ int nefe_sw_forces(const double* x, int n, const double box[3], double rcs, cons
 int nefe_sw_energy_grad(const double* x, int n, const double box[3], double rcs, const int* nbr,
                         const int* cnt, int cap, const nefe_sw_params* prm, int precision, double* f,
                         double* energy_grad, void* stream) {
+    NvtxRange nvtx_("nefe_sw_energy_grad");
     if (n < 0 || !box || cap < 1 || cap > kMaxCap || !valid_params(prm) || !energy_grad ||
         (precision != NEFE_FP32 && precision != NEFE_FP64) || (n > 0 && (!x || !nbr || !cnt)))
         return fail(NEFE_EINVAL, "nefe_sw_energy_grad: bad argument");
@@ -283,6 +288,7 @@ int nefe_sw_energy_grad(const double* x, int n, const double box[3], double rcs,
 int nefe_uf_forces(const double* x, int n, const double box[3], double rcs, double skin,
                    const nefe_uf_params* uf, int precision, double* f, double* e_atom,
                    double* energy_virial, void* stream) {
+    NvtxRange nvtx_("nefe_uf_forces");
     if (n < 0 || !box || !valid_uf(uf) || !(skin >= 0.0) || (precision != NEFE_FP32 && precision != NEFE_FP64) ||
         (n > 0 && (!x || !f)))
         return fail(NEFE_EINVAL, "nefe_uf_forces: bad argument");
@@ -329,6 +335,7 @@ int nefe_uf_forces(const double* x, int n, const double box[3], double rcs, doub
 
 int nefe_langevin_noise(uint64_t seed, uint64_t sys_id, uint64_t step, int n, int precision,
                         double* xi, void* stream) {
+    NvtxRange nvtx_("nefe_langevin_noise");
     if (n < 0 || (n > 0 && !xi) || (precision != NEFE_FP32 && precision != NEFE_FP64))
         return fail(NEFE_EINVAL, "nefe_langevin_noise: bad argument");
     launch_noise(seed, sys_id, step, n, precision, xi, (cudaStream_t)stream);

@@ -11,14 +11,13 @@
 #include "nefe_dev.h"
 #include "nefe_host.h"
 #include "nefe_launch.h"
+#include "nefe_nvtx.h"
 
 using namespace nefe;
 
 namespace {
 
 constexpr int kGraphSteps = 32;
-// launches per step (see launches_per_step)
-int launches_per_step(const nefe_ctx* c);
 
 struct HostSys {
     int n = 0;
@@ -89,6 +88,8 @@ struct nefe_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long launches = 0;
+    long graph_launches = 0;     // kernel launches in one replay of the captured graph
+    bool any_baro = false;       // some system has a barostat (k_kick_drift has work every step)
     bool profiling = false;
     std::vector<cudaEvent_t> ev0, ev1, ev2;   // around the force passes of the captured graph
     std::vector<int> chunk_tile0, chunk_ntile;
@@ -101,12 +102,6 @@ struct nefe_ctx {
 };
 
 namespace {
-
-// Per MD step: group update, kick/drift, rebuild worklist, cell count, scan, fill, list build,
-// and the two force passes per chunk (with UF systems: their list build and force kernel).
-int launches_per_step(const nefe_ctx* c) {
-    return 7 + 2 * (int)c->chunk_tile0.size() + (c->n_uf_tiles > 0 ? 2 : 0);
-}
 
 // Groups whole systems into chunks of at most `atoms` atoms (a larger system is a chunk of
 // its own).
@@ -182,9 +177,12 @@ void enqueue_forces(nefe_ctx* c, int mode, int slot = -1, int fuse = 0) {
 // epilogue (k_finish), so that the next step's k_kick_drift skips them; the last step of a
 // sequence does not, so between calls the state is at a full step as usual.
 void enqueue_step(nefe_ctx* c, int slot = -1, bool first = true, bool last = true) {
+    NvtxRange nvtx_("nefe step");
     const bool fused = c->lanes == 0;            // k_finish is the epilogue
     launch_group(c->b, c->d_groups, c->ngroups, 1, c->stream, &c->launches, fused && !first);
-    launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches, fused && !first);
+    // with every system moved by the previous epilogue there is nothing left for k_kick_drift
+    if (!(fused && !first && !c->any_baro))
+        launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches, fused && !first);
     launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
     if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
     enqueue_forces(c, FM_STEP, slot, fused && !last);
@@ -316,6 +314,7 @@ int setup(nefe_ctx* c) {
         d.rng_id = s;
         d.pair = h.pair;
         d.baro = h.baro;
+        if (h.baro != NEFE_BARO_NONE) c->any_baro = true;
         d.p_ext = h.P_GPa / kEvA3ToGPa;
         d.pdamp = h.pdamp;
         d.rcs = rcs;
@@ -486,6 +485,8 @@ int setup(nefe_ctx* c) {
     b.q = c->d_q; b.cell_of = c->d_cell_of; b.perm = c->d_perm; b.cell_start = c->d_cell_start;
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;
+    b.nbr_il = (c->cap & 3) == 0 ? 1 : 0;   // interleaved rows (the force passes read them 4 at a time)
+
     b.trace = c->d_trace;
     b.list_lanes = c->llanes;
     b.uf_nbr = c->d_uf_nbr; b.uf_cnt = c->d_uf_cnt; b.uf_F = c->d_uf_F; b.uf_tiles = c->d_uf_tiles;
@@ -684,11 +685,13 @@ int nefe_set_trace(nefe_ctx* c, int s, int every, long cap) {
 }
 
 int nefe_setup(nefe_ctx* c) {
+    NvtxRange nvtx_("nefe_setup");
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     return setup(c);
 }
 
 int nefe_run(nefe_ctx* c, long nsteps) {
+    NvtxRange nvtx_("nefe_run");
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     if (nsteps < 0) return fail(NEFE_EINVAL, "nsteps < 0");
     int rc = setup(c);
@@ -701,6 +704,7 @@ int nefe_run(nefe_ctx* c, long nsteps) {
         long before = c->launches;
         for (int k = 0; k < kGraphSteps; ++k)
             enqueue_step(c, c->profiling ? k : -1, k == 0, k == kGraphSteps - 1);
+        c->graph_launches = c->launches - before;
         c->launches = before;
         cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -709,7 +713,7 @@ int nefe_run(nefe_ctx* c, long nsteps) {
     }
     for (long f = 0; f < full; ++f) {
         NEFE_CU(cudaGraphLaunch(c->gexec, c->stream));
-        c->launches += (long)kGraphSteps * launches_per_step(c);
+        c->launches += c->graph_launches;
     }
     for (long r = 0; r < rem; ++r) enqueue_step(c, -1, r == 0, r == rem - 1);
     NEFE_CU(cudaGetLastError());
@@ -757,6 +761,7 @@ int nefe_get_pair(nefe_ctx* c, int p, double* T_coex, double* P_coex, double* la
 }
 
 int nefe_get_state(nefe_ctx* c, int s, double* x, double* v, double* box) {
+    NvtxRange nvtx_("nefe_get_state");
     int rc = check_sys(c, s);
     if (rc) return rc;
     if ((rc = setup(c))) return rc;
@@ -789,6 +794,7 @@ int nefe_get_state(nefe_ctx* c, int s, double* x, double* v, double* box) {
 }
 
 int nefe_set_state(nefe_ctx* c, int s, const double* x, const double* v) {
+    NvtxRange nvtx_("nefe_set_state");
     int rc = check_sys(c, s);
     if (rc) return rc;
     if ((rc = setup(c))) return rc;
@@ -881,6 +887,7 @@ static std::vector<Blob> blobs(nefe_ctx* c) {
 }
 
 int nefe_save(nefe_ctx* c, const char* path) {
+    NvtxRange nvtx_("nefe_save");
     if (!c || !path) return fail(NEFE_EINVAL, "NULL argument");
     int rc = setup(c);
     if (rc) return rc;
@@ -902,6 +909,7 @@ int nefe_save(nefe_ctx* c, const char* path) {
 }
 
 int nefe_load(nefe_ctx* c, const char* path) {
+    NvtxRange nvtx_("nefe_load");
     if (!c || !path) return fail(NEFE_EINVAL, "NULL argument");
     int rc = setup(c);
     if (rc) return rc;
@@ -1017,6 +1025,7 @@ static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>
 }
 
 int nefe_autotune(nefe_ctx* c) {
+    NvtxRange nvtx_("nefe_autotune");
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     int rc = setup(c);
     if (rc) return rc;
@@ -1153,6 +1162,7 @@ int nefe_set_tuning(nefe_ctx* c, int lanes) {
 }
 
 int nefe_set_state_all(nefe_ctx* c, const double* x, const double* v) {
+    NvtxRange nvtx_("nefe_set_state_all");
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     int rc = setup(c);
     if (rc) return rc;
@@ -1170,6 +1180,7 @@ int nefe_set_state_all(nefe_ctx* c, const double* x, const double* v) {
 }
 
 int nefe_get_state_all(nefe_ctx* c, double* x, double* v) {
+    NvtxRange nvtx_("nefe_get_state_all");
     if (!c) return fail(NEFE_EINVAL, "context is NULL");
     int rc = setup(c);
     if (rc) return rc;
@@ -1188,6 +1199,7 @@ int nefe_get_state_all(nefe_ctx* c, double* x, double* v) {
 }
 
 int nefe_get_results_all(nefe_ctx* c, nefe_results* out, int count) {
+    NvtxRange nvtx_("nefe_get_results_all");
     if (!c || (count > 0 && !out)) return fail(NEFE_EINVAL, "bad argument");
     if (count > (int)c->sys.size()) return fail(NEFE_EINVAL, "count above the number of systems");
     int rc = setup(c);

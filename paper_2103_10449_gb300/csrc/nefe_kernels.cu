@@ -439,22 +439,21 @@ __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int forc
     }
 }
 
-// R2: exclusive scan of the occupancy (one 256-thread block per system, 8 consecutive cells
-// per thread, so one pass covers 2048 cells); resets counts.
-__global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
+// R2: exclusive scan of system s's cell occupancy by one block (blockDim a multiple of 32, at
+// most 256; 8 consecutive cells per thread per pass); resets the counts.
+__device__ void scan_system_cells(const Bufs& b, int s) {
     constexpr int PT = 8;
-    const int s = blockIdx.x;
     const DevSys& S = b.sys[s];
     DevState& st = b.st[s];
-    if (!force_all && !st.rebuild) return;
     const int ncells = st.ncell[0] * st.ncell[1] * st.ncell[2];
     int* start = b.cell_start + S.cell0 + s;
     int* count = b.cell_count + S.cell0;
     int* cursor = b.cell_cursor + S.cell0;
     __shared__ int warp_tot[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    const int span = (int)blockDim.x * PT;
     int carry = 0;
-    for (int base = 0; base < ncells; base += 256 * PT) {
+    for (int base = 0; base < ncells; base += span) {
         const int c0 = base + (int)threadIdx.x * PT;
         int v[PT], tsum = 0;
 #pragma unroll
@@ -471,7 +470,7 @@ __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
         if (lane == 31) warp_tot[w] = incl;
         __syncthreads();
         int woff = 0, tot = 0;
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < nw; ++k) {
             if (k < w) woff += warp_tot[k];
             tot += warp_tot[k];
         }
@@ -492,6 +491,14 @@ __global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
         start[ncells] = carry;
         if (carry != S.n) atomicOr(&st.err, NEFE_ERR_CELL);
     }
+}
+
+// One 256-thread block per system; systems whose rebuild flag is clear return (all are scanned
+// with force_all).
+__global__ void __launch_bounds__(256) k_cells_scan(Bufs b, int force_all) {
+    const int s = blockIdx.x;
+    if (!force_all && !b.st[s].rebuild) return;
+    scan_system_cells(b, s);
 }
 
 // Atom index carried in the .w lane of a position vector (bit pattern in FP32, value in FP64).
@@ -545,6 +552,34 @@ __global__ void __launch_bounds__(256) k_cells_sort(Bufs b, int force_all) {
         }
     }
 }
+
+// Index of entry k of atom i's Verlet row (see Bufs::nbr_il).  The interleaved form lets the
+// lanes of a warp that take consecutive atoms read their next four entries as one contiguous
+// 512-byte request.
+__device__ __forceinline__ size_t nbr_at(const Bufs& b, int i, int k) {
+    return b.nbr_il ? ((size_t)(k >> 2) * b.ntot + i) * 4 + (k & 3) : (size_t)i * b.cap + k;
+}
+
+// Padding of an interleaved row past its mrow entries up to the next multiple of 4: atom i's
+// own image through cell offset (-1, -1, -1), at distance |(h_x, h_y, h_z)| >= sqrt(3) rcs
+// from i, so it never enters a shell (the force passes read whole groups of four).
+__device__ __forceinline__ void pad_row(const Bufs& b, int i, int mrow, int lane, int nlanes) {
+    if (!b.nbr_il) return;
+    const int end = (mrow + 3) & ~3;
+    for (int k = mrow + lane; k < end && k < b.cap; k += nlanes) b.nbr[nbr_at(b, i, k)] = i;
+}
+
+// Debug build (NEFE_DEBUG_BOUNDS, libnefe_debug.so): every atom index read from device data
+// (list entries, shell entries, UF rows) is checked before it is used; an index outside the
+// context's atoms sets NEFE_ERR_CELL in the system's error word and the access is skipped (a
+// list entry is replaced by the row's padding entry, which never enters a shell).  In the
+// normal build the check compiles away.
+#ifdef NEFE_DEBUG_BOUNDS
+#define NEFE_IN_RANGE(idx, n, errp) \
+    (((unsigned)(idx) < (unsigned)(n)) ? true : (atomicOr((errp), (unsigned)NEFE_ERR_CELL), false))
+#else
+#define NEFE_IN_RANGE(idx, n, errp) true
+#endif
 
 // Exact list criterion in FP64, the plain definition: raw = x_j - x_i, m = rint(raw/L),
 // d = raw - m L, ((d_x^2 + d_y^2) + d_z^2) < rcs^2; every operation rounded separately.
@@ -757,7 +792,6 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, unsigned (*keys)[k
     if (valid) {
         const int cap = b.cap;
         const int mrow = cnt < cap ? cnt : cap;
-        int* out = b.nbr + (size_t)i * cap;
         const uint4* row4 = reinterpret_cast<const uint4*>(keys[grp]);
         constexpr int R = 4;
         for (int a0 = 0; a0 < have; a0 += R * L) {
@@ -779,9 +813,11 @@ __device__ void nlist_item(const Bufs& b, int tile, int part, unsigned (*keys)[k
 #pragma unroll
             for (int u = 0; u < R; ++u) {
                 const int a = a0 + u * L + lane;
-                if (a < have && rk[u] < mrow) out[rk[u]] = (int)((k[u] >> 5) | ((k[u] & 31u) << kCodeShift));
+                if (a < have && rk[u] < mrow)
+                    b.nbr[nbr_at(b, i, rk[u])] = (int)((k[u] >> 5) | ((k[u] & 31u) << kCodeShift));
             }
         }
+        pad_row(b, i, mrow, lane, L);
         if (lane == 0) {
             b.cnt[i] = cnt;
             if (cnt > cap) atomicOr(&st.err, NEFE_ERR_NBR_OVERFLOW);
@@ -806,11 +842,12 @@ __global__ void __launch_bounds__(kTile, 8) k_nlist(Bufs b) {
 // R5 (list mode 0, the default): one warp per cell.  The atoms of a cell share its 27 neighbour
 // cells, so the warp walks that candidate sequence once (its 9 x-rows as pieces, 32 candidates
 // at a time, one per lane: position, image offset and index loaded once) and tests every
-// candidate against each atom of the cell in turn (the cell's atoms up to 16 at a time, their
-// positions in shared memory), with the same filter, band and exact test as above.  A ballot
-// per cell atom appends its accepted keys j * 32 + o to its shared row (the count of cell atom a
-// lives in lane a), and the rows are then ranked by atom index, one key per lane.  Every
-// candidate position is read once per neighbouring cell instead of once per neighbouring atom.
+// candidate against each atom of the cell in turn (the cell's atoms up to 8 at a time, their
+// positions in shared memory), with the same filter, band and exact test as above.  An accepted
+// key j * 32 + o is appended to the cell atom's shared row through a shared-memory counter (in
+// whatever order the lanes arrive), and the rows are then ranked by key, i.e. by atom index,
+// one key per lane, which fixes the order.  Every candidate position is read once per
+// neighbouring cell instead of once per neighbouring atom.
 constexpr int kHomeChunk = 8;             // cell atoms per walk of the candidate sequence
 template <typename T>
 struct CellListShared {
@@ -820,6 +857,10 @@ struct CellListShared {
     int4 pc[kRowPieces];                  // (first candidate, start of 2nd cell, of 3rd cell, first flat index)
     T4 po[kRowPieces];                    // offset (ox h_x, oy h_y, oz h_z) of the piece's first cell
     int code[kRowPieces];                 // cell-offset code of the piece's first cell
+    int pw[kRowPieces];                   // first flat index of each piece (the .w of pc again, as
+                                          // one int row: the search reads it without conflicts)
+    int cnt[kHomeChunk];                  // accepted count of each cell atom (append cursor)
+    unsigned sorted[kKeyRow];             // the row being written, in rank order
 };
 
 template <typename T>
@@ -883,6 +924,8 @@ __device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellList
         const int f0 = incl - len;
         const T offy = (T)oy * hy, offz = (T)oz * hz;
         const int cb = 3 * (oy + 1) + 9 * (oz + 1);
+        sh.pw[2 * lane] = f0;
+        sh.pw[2 * lane + 1] = f0 + n0;
         sh.pc[2 * lane] = make_int4(p0.x, p0.z, p0.w, f0);
         sh.po[2 * lane] = mk4(-hx, offy, offz, (T)0);
         sh.code[2 * lane] = cb;
@@ -895,19 +938,20 @@ __device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellList
     for (int h0 = 0; h0 < m; h0 += kHomeChunk) {
         const int mh = min(kHomeChunk, m - h0);
         if (lane < mh) sh.home[lane] = xc[hs + h0 + lane];
+        if (lane < kHomeChunk) sh.cnt[lane] = 0;
         __syncwarp();
-        int cnt = 0;                             // lane a: accepted count of cell atom a
         for (int t0 = 0; t0 < total; t0 += 32) {
             const int t = t0 + lane;
-            bool ok = false;
             int j = -1, o = 0;
-            T cxj = (T)0, cyj = (T)0, czj = (T)0;
+            // a candidate that is not one (past the sequence, or a bad index) sits far away, so
+            // the distance test below rejects it without a separate flag
+            T cxj = (T)1e30, cyj = (T)1e30, czj = (T)1e30;
             if (t < total) {
                 int e = 0;                       // piece of t: last entry whose flat start is <= t
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
                     const int q = e + step;
-                    if (q < kRowPieces && sh.pc[q].w <= t) e = q;
+                    if (q < kRowPieces && sh.pw[q] <= t) e = q;
                 }
                 const int4 pc = sh.pc[e];
                 const T4 po = sh.po[e];
@@ -916,37 +960,42 @@ __device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellList
                 j = unpack_index(xj.w);
                 const int inc = (p >= pc.y ? 1 : 0) + (p >= pc.z ? 1 : 0);
                 o = sh.code[e] + inc;
-                cxj = xj.x + (po.x + (T)inc * hx);
-                cyj = xj.y + po.y;
-                czj = xj.z + po.z;
-                ok = (unsigned)(j - off) < (unsigned)n;
-                if (!ok) atomicOr(&st.err, NEFE_ERR_CELL);
+                if ((unsigned)(j - off) < (unsigned)n) {
+                    cxj = xj.x + (po.x + (T)inc * hx);
+                    cyj = xj.y + po.y;
+                    czj = xj.z + po.z;
+                } else {
+                    atomicOr(&st.err, NEFE_ERR_CELL);
+                }
             }
+            // The common path is the distance test alone; the few candidates inside the upper
+            // edge of the band (about one in six) are then checked for being the atom itself,
+            // and decided by the exact FP64 criterion when they fall inside the band.  Each
+            // accepted key is appended through a shared-memory counter: the order of the keys in
+            // a row buffer does not matter, since the row is ranked by key below.
             for (int a = 0; a < mh; ++a) {
                 const T4 ha = sh.home[a];
-                const int ia = unpack_index(ha.w);
                 const T dx = cxj - ha.x, dy = cyj - ha.y, dz = czj - ha.z;
                 const T dd = dx * dx + dy * dy + dz * dz;
-                const bool cand = ok && !(j == ia && o == 13);
-                bool in = cand && dd < lo2;
-                const bool band = cand && !(dd < lo2) && dd <= hi2;
-                if (__any_sync(kAll, band)) {    // rare: decided by the exact FP64 criterion
-                    if (band) {
+                if (dd <= hi2) {
+                    const int ia = unpack_index(ha.w);
+                    bool in = !(j == ia && o == 13);
+                    if (in && !(dd < lo2)) {     // rare: decided by the exact FP64 criterion
                         double d[3];
                         in = exact_pair_in(b, st.box, ia, j, __dmul_rn(S.rcs, S.rcs), d);
                         in = in && fabs(d[0] - (double)dx) < 0.5 * st.h[0] &&
                              fabs(d[1] - (double)dy) < 0.5 * st.h[1] &&
                              fabs(d[2] - (double)dz) < 0.5 * st.h[2];
                     }
+                    if (in) {
+                        const int pos = atomicAdd(&sh.cnt[a], 1);
+                        if (pos < kMaxCap) sh.keys[a][pos] = (unsigned)j * 32u + (unsigned)o;
+                    }
                 }
-                const unsigned bal = __ballot_sync(kAll, in);
-                const int base = __shfl_sync(kAll, cnt, a);
-                const int pos = base + __popc(bal & ((1u << lane) - 1u));
-                if (in && pos < kMaxCap) sh.keys[a][pos] = (unsigned)j * 32u + (unsigned)o;
-                if (lane == a) cnt += __popc(bal);
             }
         }
         __syncwarp();
+        const int cnt = lane < kHomeChunk ? sh.cnt[lane] : 0;   // lane a: accepted count of cell atom a
         // rank each cell atom's keys by atom index (one key per lane; the row padded to a
         // multiple of 4 with the largest key and read 4 keys at a time)
         for (int a = 0; a < mh; ++a) {
@@ -957,7 +1006,6 @@ __device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellList
             if (have + lane < have4) sh.keys[a][have + lane] = 0xffffffffu;
             __syncwarp();
             const int mrow = ca < cap ? ca : cap;
-            int* out = b.nbr + (size_t)ia * cap;
             const uint4* row4 = reinterpret_cast<const uint4*>(sh.keys[a]);
             for (int k0 = 0; k0 < have; k0 += 32) {
                 const int kk = k0 + lane;
@@ -967,7 +1015,27 @@ __device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellList
                     const uint4 v = row4[z >> 2];
                     rk += (v.x < key ? 1 : 0) + (v.y < key ? 1 : 0) + (v.z < key ? 1 : 0) + (v.w < key ? 1 : 0);
                 }
-                if (kk < have && rk < mrow) out[rk] = (int)((key >> 5) | ((key & 31u) << kCodeShift));
+                if (kk < have && rk < mrow) sh.sorted[rk] = key;
+            }
+            __syncwarp();
+            // the row in rank order, four entries per lane and store (one 16-byte vector of an
+            // interleaved row, padded past mrow; consecutive lanes write consecutive entries of
+            // a row-major row)
+            for (int g = lane; 4 * g < mrow; g += 32) {
+                int v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = 4 * g + u;
+                    const unsigned key = k < mrow ? sh.sorted[k] : 0u;
+                    v[u] = k < mrow ? (int)((key >> 5) | ((key & 31u) << kCodeShift)) : ia;
+                }
+                if (b.nbr_il) {
+                    reinterpret_cast<int4*>(b.nbr)[(size_t)g * b.ntot + ia] = make_int4(v[0], v[1], v[2], v[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (4 * g + u < mrow) b.nbr[(size_t)ia * cap + 4 * g + u] = v[u];
+                }
             }
             if (lane == 0) {
                 b.cnt[ia] = ca;
@@ -1135,6 +1203,7 @@ __global__ void __launch_bounds__(kTile) k_uf(Bufs b) {
         const int* row = b.uf_nbr + (size_t)i * kUfCap;
         for (int a = 0; a < cnt; ++a) {
             const unsigned e = (unsigned)row[a];
+            if (!NEFE_IN_RANGE(e & kUfMask, b.ntot, &st.err)) continue;
             const T4 xj = X[e & kUfMask];
             const T4 oh = soff[e >> kUfShift];
             const T dx = (xj.x - xi.x) + oh.x, dy = (xj.y - xi.y) + oh.y, dz = (xj.z - xi.z) + oh.z;
@@ -1419,7 +1488,6 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
     if (valid) {
         const T4 xi = reinterpret_cast<const T4*>(b.xs)[i];
         const int ci = min(b.cnt[i], b.cap);
-        const int* row = b.nbr + (size_t)i * b.cap;
         T4* Fl = reinterpret_cast<T4*>(b.shd) + (size_t)i * kShell;
         int* Sj = b.shj + (size_t)i * kShell;
         // 1. compaction, NB row entries per lane in flight (row loads, then position gathers)
@@ -1431,7 +1499,8 @@ __global__ void __launch_bounds__(kTile) k_edges(Bufs b) {
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 const int sidx = base + u * L + lane;
-                e[u] = sidx < ci ? row[sidx] : 0;
+                e[u] = sidx < ci ? b.nbr[nbr_at(b, i, sidx)] : 0;
+                if (!NEFE_IN_RANGE(e[u] & (int)kIndexMask, b.ntot, &st.err)) e[u] = i;
             }
 #pragma unroll
             for (int u = 0; u < NB; ++u)
@@ -1621,14 +1690,23 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
     auto get_u = [&](int a) -> T4 { return a < K1 ? sh_u[a][t] : spu[a - K1]; };
     auto put_r = [&](int a, T v) { if (a < K1) sh_r[a][t] = v; else spr[a - K1] = v; };
     auto get_r = [&](int a) -> T { return a < K1 ? sh_r[a][t] : spr[a - K1]; };
-    // 1. compaction, four row entries in flight (one 16-byte load of the row when its rows are
-    // 16-byte aligned, i.e. the row capacity is a multiple of 4; entries past ci are not used)
+    // 1. compaction, four row entries in flight.  Interleaved rows (engine): one 16-byte load
+    // per four entries, contiguous across the warp, and the row is padded to a multiple of 4
+    // with entries that fail the distance test, so every entry of the last group is read
+    // unguarded.  Row-major rows: one 16-byte load when the row capacity is a multiple of 4,
+    // entries past ci not used.
     int m = 0;
+    const bool il = b.nbr_il != 0;
     const bool row4 = (b.cap & 3) == 0;
-    for (int base = 0; base < ci; base += 4) {
+    const int cend = il ? (ci + 3) & ~3 : ci;
+    const int4* row_il = reinterpret_cast<const int4*>(b.nbr) + i;
+    for (int base = 0; base < cend; base += 4) {
         int e[4];
         T4 xj[4];
-        if (row4) {
+        if (il) {
+            const int4 r4 = row_il[(size_t)(base >> 2) * b.ntot];
+            e[0] = r4.x; e[1] = r4.y; e[2] = r4.z; e[3] = r4.w;
+        } else if (row4) {
             const int4 r4 = *reinterpret_cast<const int4*>(row + base);
             e[0] = r4.x; e[1] = r4.y; e[2] = r4.z; e[3] = r4.w;
         } else {
@@ -1637,10 +1715,13 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (base + u < ci) xj[u] = pos(e[u] & (int)kIndexMask);
+            if (!NEFE_IN_RANGE(e[u] & (int)kIndexMask, b.ntot, &st.err)) e[u] = i;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (il || base + u < ci) xj[u] = pos(e[u] & (int)kIndexMask);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (base + u >= ci) continue;
+            if (!il && base + u >= ci) continue;
             const unsigned c = (unsigned)e[u] >> kCodeShift;
             const T dx = (xj[u].x - xi.x) + soff[c], dy = (xj[u].y - xi.y) + soff[32 + c],
                     dz = (xj[u].z - xi.z) + soff[64 + c];
@@ -1866,6 +1947,9 @@ __global__ void __launch_bounds__(kTile) k_gather(Bufs b) {
                         jj[u] = a < m ? b.shj[(size_t)i * kShell + a] : -1;
                     }
                 }
+#pragma unroll
+                for (int u = 0; u < NB; ++u)
+                    if (jj[u] >= 0 && !NEFE_IN_RANGE(jj[u], b.ntot, &gst.err)) jj[u] = -1;
 #pragma unroll
                 for (int u = 0; u < NB; ++u) {
                     if (jj[u] >= 0) {
@@ -2242,12 +2326,18 @@ __device__ void prepare_step(const DevSys& S, DevState& st, double dt) {
         st.phi_f[k] = (float)st.phi[k];
         st.sm1_f[k] = (float)(st.s[k] - 1.0);
         scaled = scaled || (st.s[k] != 1.0);
-        st.box[k] *= st.s[k];
-        st.h[k] = st.box[k] / (double)st.ncell[k];
-        maxrel = fmax(maxrel, fabs(st.h[k] / st.hb[k] - 1.0));
+    }
+    // With no axis scaled and the cell edge still the one of the last build, the box, h = box /
+    // ncell, h / hb = 1 and their FP32 copies are what they were: the FP64 divisions are skipped.
+    if (scaled || st.hmoved) {
+        for (int k = 0; k < 3; ++k) {
+            st.box[k] *= st.s[k];
+            st.h[k] = st.box[k] / (double)st.ncell[k];
+            maxrel = fmax(maxrel, fabs(st.h[k] / st.hb[k] - 1.0));
+        }
+        refresh_box_f(st);
     }
     st.scaled = scaled ? 1 : 0;
-    refresh_box_f(st);
     const double thr = 0.5 * (S.skin - maxrel * S.rcs);
     st.thr2 = thr > 0.0 ? thr * thr : -1.0;
     st.thr2_f = (float)st.thr2;
@@ -2464,16 +2554,38 @@ static int rebuild_grid(const Bufs& b, int items) {
     return b.rtiles ? (items < kRebuildBlocks ? items : kRebuildBlocks) : items;
 }
 
+// Launch of a kernel of the engine's step: with b.prio != 0 through cudaLaunchKernelEx with that
+// scheduling priority (lower numbers are higher priorities: the block scheduler then places
+// this grid's blocks first when slots free up), otherwise a plain launch.
+template <typename... KArgs, typename... Args>
+static void launch_k(const Bufs& b, void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+    if (b.prio == 0) {
+        kern<<<grid, block, 0, s>>>(static_cast<KArgs>(args)...);
+        return;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = b.prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
                   cudaStream_t s, long* launches) {
     if (ntiles <= 0) return;
-    if (b.rtiles) k_rebuild_list<<<1, 256, 0, s>>>(b, nsys, force_all);
+    if (b.rtiles) launch_k(b, k_rebuild_list, 1, 256, s, b, nsys, force_all);
     const int g = rebuild_grid(b, ntiles);
-    if (precision == NEFE_FP64) k_cells_count<double><<<g, kTile, 0, s>>>(b);
-    else k_cells_count<float><<<g, kTile, 0, s>>>(b);
-    k_cells_scan<<<nsys, 256, 0, s>>>(b, force_all || !b.rtiles);
-    if (precision == NEFE_FP64) k_cells_fill<double><<<g, kTile, 0, s>>>(b);
-    else k_cells_fill<float><<<g, kTile, 0, s>>>(b);
+    if (precision == NEFE_FP64) launch_k(b, k_cells_count<double>, g, kTile, s, b);
+    else launch_k(b, k_cells_count<float>, g, kTile, s, b);
+    launch_k(b, k_cells_scan, nsys, 256, s, b, force_all || !b.rtiles);
+    if (precision == NEFE_FP64) launch_k(b, k_cells_fill<double>, g, kTile, s, b);
+    else launch_k(b, k_cells_fill<float>, g, kTile, s, b);
     // the engine's list build ranks rows by atom index and never reads perm: the in-cell order
     // (fixed by the sort for the stateless cell sort) does not matter there
     if (!b.rtiles) k_cells_sort<<<nsys, 256, 0, s>>>(b, 1);
@@ -2487,20 +2599,20 @@ void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, i
     const int L = (b.list_lanes == 8 || b.list_lanes == 16 || b.list_lanes == 32) ? b.list_lanes : 0;
     if (L == 0) {
         const int g = b.rtiles ? kRebuildBlocks : max(1, min(kRebuildBlocks, ntiles * 8));
-        if (precision == NEFE_FP64) k_nlist_cell<double><<<g, kTile, 0, s>>>(b, nsys);
-        else k_nlist_cell<float><<<g, kTile, 0, s>>>(b, nsys);
+        if (precision == NEFE_FP64) launch_k(b, k_nlist_cell<double>, g, kTile, s, b, nsys);
+        else launch_k(b, k_nlist_cell<float>, g, kTile, s, b, nsys);
         if (launches) *launches += 1;
         return;
     }
     const int g = rebuild_grid(b, ntiles * L);
     if (precision == NEFE_FP64) {
-        if (L == 8) k_nlist<double, 8><<<g, kTile, 0, s>>>(b);
-        else if (L == 16) k_nlist<double, 16><<<g, kTile, 0, s>>>(b);
-        else k_nlist<double, 32><<<g, kTile, 0, s>>>(b);
+        if (L == 8) launch_k(b, k_nlist<double, 8>, g, kTile, s, b);
+        else if (L == 16) launch_k(b, k_nlist<double, 16>, g, kTile, s, b);
+        else launch_k(b, k_nlist<double, 32>, g, kTile, s, b);
     } else {
-        if (L == 8) k_nlist<float, 8><<<g, kTile, 0, s>>>(b);
-        else if (L == 16) k_nlist<float, 16><<<g, kTile, 0, s>>>(b);
-        else k_nlist<float, 32><<<g, kTile, 0, s>>>(b);
+        if (L == 8) launch_k(b, k_nlist<float, 8>, g, kTile, s, b);
+        else if (L == 16) launch_k(b, k_nlist<float, 16>, g, kTile, s, b);
+        else launch_k(b, k_nlist<float, 32>, g, kTile, s, b);
     }
     if (launches) *launches += 1;
 }
@@ -2530,19 +2642,19 @@ void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s) {
 void launch_uf_list(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches) {
     if (ntiles <= 0 || !b.uf_nbr) return;
     const int g = rebuild_grid(b, ntiles);
-    if (precision == NEFE_FP64) k_uflist<double><<<g, kTile, 0, s>>>(b);
-    else k_uflist<float><<<g, kTile, 0, s>>>(b);
+    if (precision == NEFE_FP64) launch_k(b, k_uflist<double>, g, kTile, s, b);
+    else launch_k(b, k_uflist<float>, g, kTile, s, b);
     if (launches) *launches += 1;
 }
 
 void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {
     if (ntiles <= 0 || !b.uf_nbr) return;
     if (precision == NEFE_FP64) {
-        if (mode == FM_FORCES) k_uf<double, FM_FORCES><<<ntiles, kTile, 0, s>>>(b);
-        else k_uf<double, FM_STEP><<<ntiles, kTile, 0, s>>>(b);
+        if (mode == FM_FORCES) launch_k(b, k_uf<double, FM_FORCES>, ntiles, kTile, s, b);
+        else launch_k(b, k_uf<double, FM_STEP>, ntiles, kTile, s, b);
     } else {
-        if (mode == FM_FORCES) k_uf<float, FM_FORCES><<<ntiles, kTile, 0, s>>>(b);
-        else k_uf<float, FM_STEP><<<ntiles, kTile, 0, s>>>(b);
+        if (mode == FM_FORCES) launch_k(b, k_uf<float, FM_FORCES>, ntiles, kTile, s, b);
+        else launch_k(b, k_uf<float, FM_STEP>, ntiles, kTile, s, b);
     }
     if (launches) *launches += 1;
 }
@@ -2550,8 +2662,8 @@ void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t 
 void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches,
                        int skip) {
     if (ntiles <= 0) return;
-    if (precision == NEFE_FP64) k_kick_drift<double><<<ntiles, kTile, 0, s>>>(b, mode, skip);
-    else k_kick_drift<float><<<ntiles, kTile, 0, s>>>(b, mode, skip);
+    if (precision == NEFE_FP64) launch_k(b, k_kick_drift<double>, ntiles, kTile, s, b, mode, skip);
+    else launch_k(b, k_kick_drift<float>, ntiles, kTile, s, b, mode, skip);
     if (launches) *launches += 1;
 }
 
@@ -2569,21 +2681,21 @@ static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s)
         case 0:   // one thread per atom, scatter form: FP32 only
         case 1: { // one thread per atom: FP32 only (the FP64 columns exceed the shared limit)
             if constexpr (sizeof(T) == 8) {
-                k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
+                launch_k(b, k_edges<T, 8>, ntiles * 8, kTile, s, b);
             } else {
                 const int items = ntiles * (kTile / kEdges1Threads);
-                if (lanes == 0) k_edges1<T, true><<<items, kEdges1Threads, 0, s>>>(b);
-                else k_edges1<T, false><<<items, kEdges1Threads, 0, s>>>(b);
+                if (lanes == 0) launch_k(b, k_edges1<T, true>, items, kEdges1Threads, s, b);
+                else launch_k(b, k_edges1<T, false>, items, kEdges1Threads, s, b);
             }
             break;
         }
         case 4:
-            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
-            else k_edges<T, 4><<<ntiles * 4, kTile, 0, s>>>(b);
+            if constexpr (sizeof(T) == 8) launch_k(b, k_edges<T, 8>, ntiles * 8, kTile, s, b);
+            else launch_k(b, k_edges<T, 4>, ntiles * 4, kTile, s, b);
             break;
-        case 8: k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
-        case 16: k_edges<T, 16><<<ntiles * 16, kTile, 0, s>>>(b); break;
-        default: k_edges<T, 32><<<ntiles * 32, kTile, 0, s>>>(b); break;
+        case 8: launch_k(b, k_edges<T, 8>, ntiles * 8, kTile, s, b); break;
+        case 16: launch_k(b, k_edges<T, 16>, ntiles * 16, kTile, s, b); break;
+        default: launch_k(b, k_edges<T, 32>, ntiles * 32, kTile, s, b); break;
     }
 }
 
@@ -2599,11 +2711,11 @@ void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode,
 template <typename T, int MODE>
 static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s, int fuse) {
     switch (lanes) {
-        case 0: k_finish<T, MODE><<<ntiles, kTile, 0, s>>>(b, fuse); break;
-        case 1: k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b); break;
-        case 2: k_gather<T, MODE, 2><<<ntiles * 2, kTile, 0, s>>>(b); break;
-        case 8: k_gather<T, MODE, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
-        default: k_gather<T, MODE, 4><<<ntiles * 4, kTile, 0, s>>>(b); break;
+        case 0: launch_k(b, k_finish<T, MODE>, ntiles, kTile, s, b, fuse); break;
+        case 1: launch_k(b, k_gather<T, MODE, 1>, ntiles, kTile, s, b); break;
+        case 2: launch_k(b, k_gather<T, MODE, 2>, ntiles * 2, kTile, s, b); break;
+        case 8: launch_k(b, k_gather<T, MODE, 8>, ntiles * 8, kTile, s, b); break;
+        default: launch_k(b, k_gather<T, MODE, 4>, ntiles * 4, kTile, s, b); break;
     }
 }
 
@@ -2637,7 +2749,7 @@ void launch_inject(const Bufs& b, int precision, int ntiles, const double* x, co
 void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,
                   long* launches, int carry) {
     if (ngroups <= 0) return;
-    k_group<<<ngroups, kTile, 0, s>>>(b, groups, mode, carry);
+    launch_k(b, k_group, ngroups, kTile, s, b, groups, mode, carry);
     if (launches) *launches += 1;
 }
 

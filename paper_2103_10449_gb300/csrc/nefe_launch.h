@@ -39,6 +39,11 @@ struct Bufs {
     int* nbr;
     int* cnt;
     int cap;
+    int nbr_il;              // 0: rows row-major (entry k of atom i at i cap + k); 1 (engine, cap a
+                             // multiple of 4): interleaved by 4 -- entries 4g..4g+3 of every atom
+                             // form one 16-byte vector, the vectors of consecutive atoms adjacent
+                             // (at (g ntot + i) 4 + k % 4), and each row is padded to a multiple
+                             // of 4 with entries that never pass the distance test
     int ntot;
     int tile_base;           // first tile of the launch (force passes run in L2-sized chunks)
     int* rtiles;             // rebuild worklist (tiles of flagged systems) or NULL
@@ -58,6 +63,7 @@ struct Bufs {
     void* uf_F;              // [ntot] UF force and atom energy of the step (T4)
     const int* uf_tiles;     // tiles of the UF systems (per-step UF kernel), or NULL: every tile
     int* lacc;               // [ntot][4] int32 force accumulators of the scatter form (2^-21 eV/A)
+    int prio;                // 0, or the scheduling priority of the launch (see launch_k)
 };
 
 enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };

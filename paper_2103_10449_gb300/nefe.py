@@ -159,13 +159,16 @@ def lib_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Loads libnefe.so (building it with nvcc first when missing or stale)."""
+    """Loads libnefe.so (building it with nvcc first when missing or stale).  With the
+    environment variable NEFE_DEBUG_BOUNDS=1 the process loads libnefe_debug.so instead, the
+    same sources built with index checks on every atom index read from device data."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing and _build.needs_build():
-        _build.build()
+    debug = os.environ.get("NEFE_DEBUG_BOUNDS", "0") == "1"
+    path = _build.LIB_DEBUG if debug else _build.LIB
+    if build_if_missing and _build.needs_build(debug):
+        _build.build(debug=debug)
     if not os.path.exists(path):
         raise NefeError(NEFE_ECUDA, f"{path} is missing: run paper_2103_10449_gb300.build")
     L = ctypes.CDLL(path)

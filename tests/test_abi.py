@@ -29,6 +29,17 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert set(names) == set(N.SIGNATURES) | {"nefe_last_error"}
 
 
+def test_debug_bounds_library_builds_and_exports_every_declared_symbol():
+    """The debug flavour (index checks on every atom index read from device data) is the same
+    sources with NEFE_DEBUG_BOUNDS: it builds beside the normal library and exports the same
+    C ABI."""
+    path = B.build(debug=True)
+    assert os.path.basename(path) == "libnefe_debug.so" and os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert missing == []
+
+
 def test_host_only_calls_work_without_gpu():
     p = N.nefe_sw_params_silicon()
     assert (p.eps, p.sigma, p.A, p.B, p.p, p.q, p.a, p.lambda3, p.gamma) == (

@@ -4,6 +4,9 @@ The per-system error word must stay clear (no NaN, no list or cell inconsistency
 thermostat must hold the temperature, and the list must keep every in-cutoff pair.
 """
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -59,3 +62,40 @@ def test_list_holds_every_pair_inside_the_cutoff_after_a_long_run():
     ctx.close()
     e_o = O.sw_energy(x, box)[0]
     assert r["U"] == pytest.approx(e_o, rel=1e-10)
+
+
+_DEBUG_RUN = r"""
+import sys, math
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2103_10449_gb300 import inputs as I, nefe as N
+x, box = I.diamond(3, 3, 3)
+sv = math.sqrt(8.617333262e-5 * 1000.0 / (28.0855 * 1.66053906660e-23 / 1.602176634e-19))
+ctx = N.Context(precision=N.NEFE_FP32, skin=0.5, nbr_cap=48)
+s = ctx.add_system(x, box, v=I.gaussian_velocities(len(x), sv, 71), r0=x)
+ctx.set_thermostat(s, 1000.0, 0.1, 72)
+ctx.set_schedule(s, N.NEFE_SCHED_FL, nsteps=400, k_E=5.0)
+ctx.set_tuning(0)
+ctx.run(101)
+r = ctx.results(s)
+xs, _, _ = ctx.get_state(s)
+print(N._build.LIB_DEBUG if N.load()._name.endswith("libnefe_debug.so") else N._build.LIB)
+print(repr(r["W"]), r["error"], repr(float(np.abs(xs).sum())))
+"""
+
+
+def test_debug_bounds_build_runs_the_same_trajectory():
+    """libnefe_debug.so (index checks on every atom index read from device data) runs a scatter-
+    form switching run bit for bit like the normal library and raises no error bit."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for flag in ("0", "1"):
+        env = dict(os.environ, NEFE_DEBUG_BOUNDS=flag)
+        p = subprocess.run([sys.executable, "-c", _DEBUG_RUN, root], env=env, capture_output=True, text=True,
+                           timeout=900)
+        assert p.returncode == 0, p.stderr[-2000:]
+        lib, vals = p.stdout.strip().splitlines()[-2:]
+        assert lib.endswith("libnefe_debug.so" if flag == "1" else "libnefe.so")
+        out[flag] = vals.split()
+    assert out["0"] == out["1"]
+    assert out["1"][1] == "0"
