@@ -1304,15 +1304,16 @@ __device__ __forceinline__ void comp_add(T& hi, T& lo, T d) {
 // *flag) and the thermostat noise of step kstep (stored, and returned in z).  dh, dl: the atom's
 // displacement, updated in place.  Shared by k_kick_drift and by the epilogue that moves the
 // atoms for the next step (systems without a barostat), so both do the same operations.
+// xa: the atom's mirror at the last build (loaded by the caller together with its other operands).
 template <typename T>
 __device__ __forceinline__ void drift_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
-                                           const T (&vk)[3], bool move, T (&dh)[3], T (&dl)[3],
-                                           int flag_set, int* flag, unsigned long long kstep, T (&z)[3]) {
+                                           const typename V4<T>::t& xa, const T (&vk)[3], bool move,
+                                           T (&dh)[3], T (&dl)[3], int flag_set, int* flag,
+                                           unsigned long long kstep, T (&z)[3]) {
     using T4 = typename V4<T>::t;
     const size_t N = b.ntot;
     T* DH = reinterpret_cast<T*>(b.dhi);
     T* DL = reinterpret_cast<T*>(b.dlo);
-    const T4 xa = reinterpret_cast<const T4*>(b.xa)[i];
     const T xav[3] = {xa.x, xa.y, xa.z};
     const bool scaled = st.scaled != 0, hmoved = st.hmoved != 0;
     int4 q = make_int4(0, 0, 0, 0);
@@ -1366,6 +1367,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode, int skip
         T* V = reinterpret_cast<T*>(b.v);
         const T* DH = reinterpret_cast<const T*>(b.dhi);
         const T* DL = reinterpret_cast<const T*>(b.dlo);
+        const T4 xa = reinterpret_cast<const T4*>(b.xa)[i];
         T dh[3], dl[3], vk[3] = {(T)0, (T)0, (T)0};
         for (int k = 0; k < 3; ++k) {
             dh[k] = DH[k * N + i];
@@ -1380,7 +1382,7 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode, int skip
                 V[k * N + i] = vk[k];
             }
         }
-        drift_atom<T>(b, S, st, i, vk, mode == 1, dh, dl, st.rebuild, &st.rebuild, (unsigned long long)st.k,
+        drift_atom<T>(b, S, st, i, xa, vk, mode == 1, dh, dl, st.rebuild, &st.rebuild, (unsigned long long)st.k,
                       xs_sum);
     }
     block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &st.err);
@@ -1825,14 +1827,13 @@ __device__ __forceinline__ void edges1_atom(const Bufs& b, const SWc<T>& P, DevS
 }
 
 template <typename T, bool SCATTER>
-__device__ __forceinline__ void edges1_item(const Bufs& b, int item, typename V4<T>::t (*sh_u)[kEdges1Threads],
+__device__ __forceinline__ void edges1_item(const Bufs& b, int tile, int part, typename V4<T>::t (*sh_u)[kEdges1Threads],
                                             T (*sh_r)[kEdges1Threads], int (*sh_j)[kEdges1Threads],
                                             T* soff) {
     using T4 = typename V4<T>::t;
     constexpr int NT = kEdges1Threads;
     // 20 bytes per shell entry and thread (occupancy is bound by this table):
     constexpr int K1 = kShell1Shared, KS = kShell1 - kShell1Shared;
-    const int tile = item / (kTile / NT) + b.tile_base, part = item % (kTile / NT);
     const TileAtom ta = tile_of(b, tile);
     const DevSys& S = b.sys[ta.sys];
     DevState& st = b.st[ta.sys];
@@ -1857,7 +1858,8 @@ __global__ void __launch_bounds__(kEdges1Threads, 16) k_edges1(Bufs b) {
     __shared__ T sh_r[kEdges1K1][kEdges1Threads];    // r
     __shared__ int sh_j[SCATTER ? kEdges1K1 : 1][kEdges1Threads];   // shell atom indices (scatter form)
     __shared__ T soff[3 * 32];
-    edges1_item<T, SCATTER>(b, blockIdx.x, sh_u, sh_r, sh_j, soff);
+    constexpr int IPT = kTile / kEdges1Threads;  // work items per tile
+    edges1_item<T, SCATTER>(b, (int)blockIdx.x / IPT + b.tile_base, (int)blockIdx.x % IPT, sh_u, sh_r, sh_j, soff);
 }
 
 // Force pass B, L lanes per atom:
@@ -2171,6 +2173,8 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b, int fuse) {
             pv[0] = V[i]; pv[1] = V[N + i]; pv[2] = V[2 * N + i];
         }
         if (thermo) z = reinterpret_cast<const T4*>(b.xi)[i];
+        T4 xa = mk4((T)0, (T)0, (T)0, (T)0);
+        if (fz) xa = reinterpret_cast<const T4*>(b.xa)[i];
         if (sw) *a4 = make_int4(0, 0, 0, 0);
         const T pd[3] = {d0.x + dh[0] + dl[0], d0.y + dh[1] + dl[1], d0.z + dh[2] + dl[2]};
         const T pz[3] = {z.x, z.y, z.z};
@@ -2188,7 +2192,8 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b, int fuse) {
                 vk[k] = vo[k] + ck * Fo[k];
                 V[k * N + i] = vk[k];
             }
-            drift_atom<T>(b, S, st, i, vk, true, dh, dl, 0, &gst.rebuild_next, (unsigned long long)st.k + 1ULL, zn);
+            drift_atom<T>(b, S, st, i, xa, vk, true, dh, dl, 0, &gst.rebuild_next, (unsigned long long)st.k + 1ULL,
+                          zn);
         }
     }
     block_sum_to_acc<T, 14>(red, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_UINT, &gst.err);
@@ -2554,38 +2559,16 @@ static int rebuild_grid(const Bufs& b, int items) {
     return b.rtiles ? (items < kRebuildBlocks ? items : kRebuildBlocks) : items;
 }
 
-// Launch of a kernel of the engine's step: with b.prio != 0 through cudaLaunchKernelEx with that
-// scheduling priority (lower numbers are higher priorities: the block scheduler then places
-// this grid's blocks first when slots free up), otherwise a plain launch.
-template <typename... KArgs, typename... Args>
-static void launch_k(const Bufs& b, void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
-    if (b.prio == 0) {
-        kern<<<grid, block, 0, s>>>(static_cast<KArgs>(args)...);
-        return;
-    }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributePriority;
-    at[0].val.priority = b.prio;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 void launch_cells(const Bufs& b, int precision, int ntiles, int nsys, int force_all,
                   cudaStream_t s, long* launches) {
     if (ntiles <= 0) return;
-    if (b.rtiles) launch_k(b, k_rebuild_list, 1, 256, s, b, nsys, force_all);
+    if (b.rtiles) k_rebuild_list<<<1, 256, 0, s>>>(b, nsys, force_all);
     const int g = rebuild_grid(b, ntiles);
-    if (precision == NEFE_FP64) launch_k(b, k_cells_count<double>, g, kTile, s, b);
-    else launch_k(b, k_cells_count<float>, g, kTile, s, b);
-    launch_k(b, k_cells_scan, nsys, 256, s, b, force_all || !b.rtiles);
-    if (precision == NEFE_FP64) launch_k(b, k_cells_fill<double>, g, kTile, s, b);
-    else launch_k(b, k_cells_fill<float>, g, kTile, s, b);
+    if (precision == NEFE_FP64) k_cells_count<double><<<g, kTile, 0, s>>>(b);
+    else k_cells_count<float><<<g, kTile, 0, s>>>(b);
+    k_cells_scan<<<nsys, 256, 0, s>>>(b, force_all || !b.rtiles);
+    if (precision == NEFE_FP64) k_cells_fill<double><<<g, kTile, 0, s>>>(b);
+    else k_cells_fill<float><<<g, kTile, 0, s>>>(b);
     // the engine's list build ranks rows by atom index and never reads perm: the in-cell order
     // (fixed by the sort for the stateless cell sort) does not matter there
     if (!b.rtiles) k_cells_sort<<<nsys, 256, 0, s>>>(b, 1);
@@ -2599,20 +2582,20 @@ void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, i
     const int L = (b.list_lanes == 8 || b.list_lanes == 16 || b.list_lanes == 32) ? b.list_lanes : 0;
     if (L == 0) {
         const int g = b.rtiles ? kRebuildBlocks : max(1, min(kRebuildBlocks, ntiles * 8));
-        if (precision == NEFE_FP64) launch_k(b, k_nlist_cell<double>, g, kTile, s, b, nsys);
-        else launch_k(b, k_nlist_cell<float>, g, kTile, s, b, nsys);
+        if (precision == NEFE_FP64) k_nlist_cell<double><<<g, kTile, 0, s>>>(b, nsys);
+        else k_nlist_cell<float><<<g, kTile, 0, s>>>(b, nsys);
         if (launches) *launches += 1;
         return;
     }
     const int g = rebuild_grid(b, ntiles * L);
     if (precision == NEFE_FP64) {
-        if (L == 8) launch_k(b, k_nlist<double, 8>, g, kTile, s, b);
-        else if (L == 16) launch_k(b, k_nlist<double, 16>, g, kTile, s, b);
-        else launch_k(b, k_nlist<double, 32>, g, kTile, s, b);
+        if (L == 8) k_nlist<double, 8><<<g, kTile, 0, s>>>(b);
+        else if (L == 16) k_nlist<double, 16><<<g, kTile, 0, s>>>(b);
+        else k_nlist<double, 32><<<g, kTile, 0, s>>>(b);
     } else {
-        if (L == 8) launch_k(b, k_nlist<float, 8>, g, kTile, s, b);
-        else if (L == 16) launch_k(b, k_nlist<float, 16>, g, kTile, s, b);
-        else launch_k(b, k_nlist<float, 32>, g, kTile, s, b);
+        if (L == 8) k_nlist<float, 8><<<g, kTile, 0, s>>>(b);
+        else if (L == 16) k_nlist<float, 16><<<g, kTile, 0, s>>>(b);
+        else k_nlist<float, 32><<<g, kTile, 0, s>>>(b);
     }
     if (launches) *launches += 1;
 }
@@ -2642,19 +2625,19 @@ void launch_decode_ev(const long long* acc, double* out7, cudaStream_t s) {
 void launch_uf_list(const Bufs& b, int precision, int ntiles, cudaStream_t s, long* launches) {
     if (ntiles <= 0 || !b.uf_nbr) return;
     const int g = rebuild_grid(b, ntiles);
-    if (precision == NEFE_FP64) launch_k(b, k_uflist<double>, g, kTile, s, b);
-    else launch_k(b, k_uflist<float>, g, kTile, s, b);
+    if (precision == NEFE_FP64) k_uflist<double><<<g, kTile, 0, s>>>(b);
+    else k_uflist<float><<<g, kTile, 0, s>>>(b);
     if (launches) *launches += 1;
 }
 
 void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches) {
     if (ntiles <= 0 || !b.uf_nbr) return;
     if (precision == NEFE_FP64) {
-        if (mode == FM_FORCES) launch_k(b, k_uf<double, FM_FORCES>, ntiles, kTile, s, b);
-        else launch_k(b, k_uf<double, FM_STEP>, ntiles, kTile, s, b);
+        if (mode == FM_FORCES) k_uf<double, FM_FORCES><<<ntiles, kTile, 0, s>>>(b);
+        else k_uf<double, FM_STEP><<<ntiles, kTile, 0, s>>>(b);
     } else {
-        if (mode == FM_FORCES) launch_k(b, k_uf<float, FM_FORCES>, ntiles, kTile, s, b);
-        else launch_k(b, k_uf<float, FM_STEP>, ntiles, kTile, s, b);
+        if (mode == FM_FORCES) k_uf<float, FM_FORCES><<<ntiles, kTile, 0, s>>>(b);
+        else k_uf<float, FM_STEP><<<ntiles, kTile, 0, s>>>(b);
     }
     if (launches) *launches += 1;
 }
@@ -2662,8 +2645,8 @@ void launch_uf(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t 
 void launch_kick_drift(const Bufs& b, int precision, int ntiles, int mode, cudaStream_t s, long* launches,
                        int skip) {
     if (ntiles <= 0) return;
-    if (precision == NEFE_FP64) launch_k(b, k_kick_drift<double>, ntiles, kTile, s, b, mode, skip);
-    else launch_k(b, k_kick_drift<float>, ntiles, kTile, s, b, mode, skip);
+    if (precision == NEFE_FP64) k_kick_drift<double><<<ntiles, kTile, 0, s>>>(b, mode, skip);
+    else k_kick_drift<float><<<ntiles, kTile, 0, s>>>(b, mode, skip);
     if (launches) *launches += 1;
 }
 
@@ -2681,21 +2664,21 @@ static void edges_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s)
         case 0:   // one thread per atom, scatter form: FP32 only
         case 1: { // one thread per atom: FP32 only (the FP64 columns exceed the shared limit)
             if constexpr (sizeof(T) == 8) {
-                launch_k(b, k_edges<T, 8>, ntiles * 8, kTile, s, b);
+                k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
             } else {
                 const int items = ntiles * (kTile / kEdges1Threads);
-                if (lanes == 0) launch_k(b, k_edges1<T, true>, items, kEdges1Threads, s, b);
-                else launch_k(b, k_edges1<T, false>, items, kEdges1Threads, s, b);
+                if (lanes == 0) k_edges1<T, true><<<items, kEdges1Threads, 0, s>>>(b);
+                else k_edges1<T, false><<<items, kEdges1Threads, 0, s>>>(b);
             }
             break;
         }
         case 4:
-            if constexpr (sizeof(T) == 8) launch_k(b, k_edges<T, 8>, ntiles * 8, kTile, s, b);
-            else launch_k(b, k_edges<T, 4>, ntiles * 4, kTile, s, b);
+            if constexpr (sizeof(T) == 8) k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b);
+            else k_edges<T, 4><<<ntiles * 4, kTile, 0, s>>>(b);
             break;
-        case 8: launch_k(b, k_edges<T, 8>, ntiles * 8, kTile, s, b); break;
-        case 16: launch_k(b, k_edges<T, 16>, ntiles * 16, kTile, s, b); break;
-        default: launch_k(b, k_edges<T, 32>, ntiles * 32, kTile, s, b); break;
+        case 8: k_edges<T, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
+        case 16: k_edges<T, 16><<<ntiles * 16, kTile, 0, s>>>(b); break;
+        default: k_edges<T, 32><<<ntiles * 32, kTile, 0, s>>>(b); break;
     }
 }
 
@@ -2711,11 +2694,11 @@ void launch_edges(const Bufs& b, int precision, int lanes, int ntiles, int mode,
 template <typename T, int MODE>
 static void gather_dispatch(const Bufs& b, int lanes, int ntiles, cudaStream_t s, int fuse) {
     switch (lanes) {
-        case 0: launch_k(b, k_finish<T, MODE>, ntiles, kTile, s, b, fuse); break;
-        case 1: launch_k(b, k_gather<T, MODE, 1>, ntiles, kTile, s, b); break;
-        case 2: launch_k(b, k_gather<T, MODE, 2>, ntiles * 2, kTile, s, b); break;
-        case 8: launch_k(b, k_gather<T, MODE, 8>, ntiles * 8, kTile, s, b); break;
-        default: launch_k(b, k_gather<T, MODE, 4>, ntiles * 4, kTile, s, b); break;
+        case 0: k_finish<T, MODE><<<ntiles, kTile, 0, s>>>(b, fuse); break;
+        case 1: k_gather<T, MODE, 1><<<ntiles, kTile, 0, s>>>(b); break;
+        case 2: k_gather<T, MODE, 2><<<ntiles * 2, kTile, 0, s>>>(b); break;
+        case 8: k_gather<T, MODE, 8><<<ntiles * 8, kTile, 0, s>>>(b); break;
+        default: k_gather<T, MODE, 4><<<ntiles * 4, kTile, 0, s>>>(b); break;
     }
 }
 
@@ -2749,7 +2732,7 @@ void launch_inject(const Bufs& b, int precision, int ntiles, const double* x, co
 void launch_group(const Bufs& b, const DevGroup* groups, int ngroups, int mode, cudaStream_t s,
                   long* launches, int carry) {
     if (ngroups <= 0) return;
-    launch_k(b, k_group, ngroups, kTile, s, b, groups, mode, carry);
+    k_group<<<ngroups, kTile, 0, s>>>(b, groups, mode, carry);
     if (launches) *launches += 1;
 }
 
