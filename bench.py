@@ -175,8 +175,10 @@ class FLEngine:
         self.ctx, self.natoms = build_context(N, hi - lo, N.NEFE_FP32, stream=self.stream, skin=args.skin, first=lo)
         self.ctx.run(args.equil)
         if args.tuning:
-            la, lb = (int(v) for v in args.tuning.split(","))
-            self.ctx.set_tuning(la, lb)
+            t = [int(v) for v in args.tuning.split(",")]
+            self.ctx.set_tuning(t[0], t[1])
+            if len(t) > 2:
+                self.ctx.set_rebuild_policy(t[2])
         else:
             self.ctx.autotune()
 
@@ -589,7 +591,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
     ap.add_argument("--skin", type=float, default=SKIN, help="Verlet skin (A) of the timed context")
     ap.add_argument("--tuning", default=None,
-                    help="pass A,pass B lanes per atom instead of autotuning (e.g. to profile a chosen configuration)")
+                    help="pass A,pass B lanes per atom[,rebuild policy] instead of autotuning (e.g. to profile a chosen "
+                         "configuration)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -674,7 +677,7 @@ def main():
                 "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak,
                 "step_bytes_per_atom_step": STEP_BYTES,
                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "lanes_per_atom": lanes[0],
-                "lanes_pass_a_pass_b_list": lanes}
+                "lanes_pass_a_pass_b_list": lanes, "rebuild_all_systems": ctx.rebuild_policy()}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,

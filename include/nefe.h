@@ -401,10 +401,11 @@ NEFE_API int nefe_load(nefe_ctx* ctx, const char* path);
 
 /* Times the variants of both force passes on the current state and keeps the fastest:
  * pass A with 1 (one thread per atom), 4, 8, 16 or 32 lanes per atom (FP64: 8, 16, 32),
- * pass B with 1, 2, 4 or 8 lanes per atom, the list build with 8, 16 or 32.  Each force pass
- * is first timed alone; then the two fastest pass-A variants with every pass-B variant, and
- * with the best pair each list-build variant, run as real steps on a device snapshot of the
- * state, restored afterwards (the run
+ * pass B with 1, 2, 4 or 8 lanes per atom, the list build with 8, 16 or 32, and the rebuild
+ * policy (nefe_set_rebuild_policy).  Each force pass is first timed alone; then the two fastest
+ * pass-A variants with every pass-B variant, and with the best pair each list-build variant and
+ * each rebuild policy, run as real steps on a device snapshot of the state, restored afterwards
+ * (the run
  * continues bit for bit as without the call; the snapshot needs about as much free device
  * memory as the state, and without it the kernel-level choice stands).  nefe_get_tuning
  * reports pass A's lanes and the time per MD step of the chosen pair (kernel-level: the two
@@ -418,6 +419,16 @@ NEFE_API int nefe_get_lanes(nefe_ctx* ctx, int lanes[3]);
 NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
 /* Fixes the list build's form: 0 = one warp per cell (the default), or 8, 16, 32 lanes per atom. */
 NEFE_API int nefe_set_list_tuning(nefe_ctx* ctx, int lanes_per_atom);
+/* Rebuild policy of the Verlet lists (the skin criterion of the list, Sec. 4's MD setup; the
+ * paper itself does not discuss lists).  all = 0: each system rebuilds when one of its own atoms
+ * has moved more than skin/2 since its last build.  all = 1: on a step where any system needs
+ * a rebuild, every system rebuilds -- lists are rebuilt earlier than needed, which never
+ * changes what the force passes compute (trajectories differ from policy 0 only by the
+ * rounding of the position anchor), and the batch then runs one full-width build instead of
+ * many narrow ones.  nefe_autotune times both in real steps and keeps the faster.
+ * NEFE_EINVAL for other values.  nefe_get_rebuild_policy: the policy in use. */
+NEFE_API int nefe_set_rebuild_policy(nefe_ctx* ctx, int all);
+NEFE_API int nefe_get_rebuild_policy(nefe_ctx* ctx, int* all);
 
 /* Batched state transfer for every system at once: host (Ntot, 3) arrays, systems in the
  * order they were added (Ntot = sum of their n).  One host<->device copy each, the layout

@@ -84,6 +84,7 @@ struct nefe_ctx {
                              // thread per atom in the scatter form, whose pass B is k_finish)
     int glanes = 4;          // pass B lanes per atom (1, 2, 4, 8)
     int llanes = 0;          // list build: 0 one warp per cell; 8, 16, 32 lanes per atom
+    int rebuild_all = 0;     // rebuild policy (nefe_set_rebuild_policy)
     double tune_us = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -486,6 +487,7 @@ int setup(nefe_ctx* c) {
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;
     b.nbr_il = (c->cap & 3) == 0 ? 1 : 0;   // interleaved rows (the force passes read them 4 at a time)
+    b.rebuild_all = c->rebuild_all;
 
     b.trace = c->d_trace;
     b.list_lanes = c->llanes;
@@ -1009,6 +1011,28 @@ static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>
     }
     c->llanes = best_l;
     c->b.list_lanes = best_l;
+    // then the rebuild policy with the chosen lanes (its effect too is seen only in real steps)
+    int best_r = c->rebuild_all;
+    if (rc == NEFE_OK) {
+        const int other = 1 - c->rebuild_all;
+        c->lanes = best_a;
+        c->glanes = best_b;
+        c->b.rebuild_all = other;
+        drop_graph(c);
+        if ((rc = nefe_run(c, kGraphSteps)) == NEFE_OK) {
+            cudaEventRecord(e0, c->stream);
+            if ((rc = nefe_run(c, 2 * kGraphSteps)) == NEFE_OK) {
+                cudaEventRecord(e1, c->stream);
+                float ms = 1e30f;
+                if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                const double us = 1000.0 * ms / (2 * kGraphSteps);
+                if (us < best) { best = us; best_r = other; }
+                copy(false);
+            }
+        }
+    }
+    c->rebuild_all = best_r;
+    c->b.rebuild_all = best_r;
     cudaStreamSynchronize(c->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1331,6 +1355,21 @@ int nefe_set_gather_tuning(nefe_ctx* c, int lanes) {
         return fail(NEFE_EINVAL, "pass B supports 1, 2, 4 or 8 lanes per atom");
     if (lanes != c->glanes) drop_graph(c);
     c->glanes = lanes;
+    return NEFE_OK;
+}
+
+int nefe_set_rebuild_policy(nefe_ctx* c, int all) {
+    if (!c) return fail(NEFE_EINVAL, "context is NULL");
+    if (all != 0 && all != 1) return fail(NEFE_EINVAL, "rebuild policy must be 0 or 1");
+    if (c->b.rebuild_all != all) drop_graph(c);   // the policy is captured in the step graph
+    c->rebuild_all = all;
+    c->b.rebuild_all = all;
+    return NEFE_OK;
+}
+
+int nefe_get_rebuild_policy(nefe_ctx* c, int* all) {
+    if (!c || !all) return fail(NEFE_EINVAL, "NULL argument");
+    *all = c->rebuild_all;
     return NEFE_OK;
 }
 

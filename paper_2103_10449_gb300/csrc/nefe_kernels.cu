@@ -375,9 +375,19 @@ __global__ void __launch_bounds__(kTile) k_cells_count(Bufs b) {
 // only when the box or the list radius differ from the ones the grid was last computed for
 // (the FP64 divisions are skipped for every system at fixed volume).
 // Tile order in the list does not matter: every tile is processed independently.
+// With b.rebuild_all, a step on which any system's flag is set rebuilds every system (the flags
+// of all are set here, so the later rebuild kernels see them): rebuilding a list early never
+// changes what the force passes compute, and one build over the whole batch runs its kernels at
+// full width where many small builds, one per step, each pay their latency.
 __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
+    if (b.rebuild_all && !force_all) {
+        int any = 0;
+        for (int s = threadIdx.x; s < nsys; s += blockDim.x) any |= b.st[s].rebuild;
+        if (__syncthreads_or(any))
+            for (int s = threadIdx.x; s < nsys; s += blockDim.x) b.st[s].rebuild = 1;
+    }
     __syncthreads();
     for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
         DevState& st = b.st[s];

@@ -63,6 +63,8 @@ struct Bufs {
     void* uf_F;              // [ntot] UF force and atom energy of the step (T4)
     const int* uf_tiles;     // tiles of the UF systems (per-step UF kernel), or NULL: every tile
     int* lacc;               // [ntot][4] int32 force accumulators of the scatter form (2^-21 eV/A)
+    int rebuild_all;         // engine: when any system's list is stale, every system rebuilds (one
+                             // full-width build instead of many narrow ones)
 };
 
 enum ForceMode { FM_FORCES = 0, FM_SETUP = 1, FM_STEP = 2 };

@@ -141,6 +141,8 @@ SIGNATURES = {
     "nefe_set_gather_tuning": [_vp, ctypes.c_int],
     "nefe_get_lanes": [_vp, _c_int_p],
     "nefe_set_list_tuning": [_vp, ctypes.c_int],
+    "nefe_set_rebuild_policy": [_vp, ctypes.c_int],
+    "nefe_get_rebuild_policy": [_vp, _c_int_p],
     "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
     "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
     "nefe_get_state_all": [_vp, _c_dbl_p, _c_dbl_p],
@@ -413,6 +415,15 @@ class Context:
             _check(self._L.nefe_set_gather_tuning(self.h, int(gather_lanes)))
         if list_lanes is not None:
             _check(self._L.nefe_set_list_tuning(self.h, int(list_lanes)))
+
+    def set_rebuild_policy(self, all_systems):
+        """1: every system rebuilds its list on a step where any system needs it; 0: each on its own."""
+        _check(self._L.nefe_set_rebuild_policy(self.h, int(all_systems)))
+
+    def rebuild_policy(self):
+        out = ctypes.c_int()
+        _check(self._L.nefe_get_rebuild_policy(self.h, ctypes.byref(out)))
+        return out.value
 
     def set_state_all(self, x=None, v=None):
         """x, v: host (Ntot, 3) float64 arrays (pinned memory makes the copy faster)."""

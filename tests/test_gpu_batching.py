@@ -33,7 +33,11 @@ def N():
     return nefe
 
 
-def test_uneven_batch_matches_oracle_per_system(N):
+@pytest.mark.parametrize("rebuild_all", [0, 1])
+def test_uneven_batch_matches_oracle_per_system(N, rebuild_all):
+    """With rebuild_all every system rebuilds its list on a step where any system needs one: the
+    lists are then rebuilt earlier than needed, which must leave every trajectory on the oracle's
+    (which has no list at all), and every system counts the same builds."""
     T = 400.0
     p0 = 10.0
     xa1, ba1 = I.diamond(2, 2, 2)
@@ -60,12 +64,17 @@ def test_uneven_batch_matches_oracle_per_system(N):
     ctx.set_schedule(4, N.NEFE_SCHED_FL, direction=-1, nsteps=300, k_E=5.0)
     ctx.set_barostat(5, N.NEFE_BARO_ISO, 1.0, 0.5)
     ctx.set_schedule(5, N.NEFE_SCHED_RS, nsteps=200, lambda_f=0.5, P_GPa=1.0)
+    ctx.set_rebuild_policy(rebuild_all)
     ctx.run(NST)
     res = ctx.results_all()
     states = [ctx.get_state(k) for k in range(len(pos))]
     pairs = [ctx.pair(pid_t), ctx.pair(pid_p)]
+    builds = [ctx.list_stats(k)[2] for k in range(len(pos))]
+    assert ctx.rebuild_policy() == rebuild_all
     ctx.close()
     assert all(r["error"] == 0 for r in res)
+    if rebuild_all:
+        assert len(set(builds)) == 1 and builds[0] >= 1, builds
 
     def sysk(k, **kw):
         return O.System(x=pos[k].copy(), v=vel[k].copy(), box=boxes[k].copy(), T=T, tdamp=0.1, seed=seeds[k],

@@ -48,6 +48,30 @@ def test_batched_frenkel_ladd_long_run_stays_physical():
     ctx.close()
 
 
+def test_rebuild_all_policy_rebuilds_together_and_keeps_forces_exact():
+    """Policy rebuild_all: on a step where one system's list is stale every system rebuilds.
+    The systems then count the same builds, more than under the per-system policy, and the
+    engine's SW energy of each final state equals the oracle's brute-force energy of it."""
+    from oracle import oracle as O
+    from paper_2103_10449_gb300 import nefe as N
+    builds = {}
+    for pol in (0, 1):
+        ctx, n = _ctx(N, 3, precision=0)
+        ctx.set_tuning(0)
+        ctx.set_rebuild_policy(pol)
+        ctx.run(400)
+        builds[pol] = [ctx.list_stats(s)[2] for s in range(3)]
+        if pol == 1:
+            for s in range(3):
+                x, _, box = ctx.get_state(s)
+                r = ctx.results(s)
+                assert r["error"] == 0
+                assert r["U"] == pytest.approx(O.sw_energy(x, box)[0], rel=1e-5)
+        ctx.close()
+    assert len(set(builds[1])) == 1 and builds[1][0] > 5
+    assert builds[1][0] >= max(builds[0])
+
+
 def test_list_holds_every_pair_inside_the_cutoff_after_a_long_run():
     """Verlet guarantee: each pair closer than a*sigma at the current positions is in the
     engine's list.  The engine's SW energy of the state it reports after 2000 steps must equal

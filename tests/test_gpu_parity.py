@@ -305,7 +305,8 @@ def test_thread_per_atom_pass_a_with_spilled_shells(N, lanes):
 
 def test_autotune_leaves_the_run_unchanged(N):
     """The autotuner's step-level timing runs on a snapshot that it restores: a run that
-    autotunes midway equals, bit for bit, one that sets the chosen lanes by hand."""
+    autotunes midway equals, bit for bit, one that sets the chosen lanes and rebuild policy by
+    hand."""
     from paper_2103_10449_gb300 import nefe
     x0, box = I.diamond(4, 4, 4)
     v0 = I.gaussian_velocities(len(x0), _sv(1000.0), 91)
@@ -321,6 +322,7 @@ def test_autotune_leaves_the_run_unchanged(N):
     a.run(64)
     a.autotune()
     la = a.lanes()
+    pol = a.rebuild_policy()
     a.run(64)
     ra = a.results_all()
     xa = [a.get_state(s)[0] for s in range(3)]
@@ -328,6 +330,7 @@ def test_autotune_leaves_the_run_unchanged(N):
     b = make()
     b.run(64)
     b.set_tuning(la[0], la[1], la[2])
+    b.set_rebuild_policy(pol)
     b.run(64)
     rb = b.results_all()
     xb = [b.get_state(s)[0] for s in range(3)]
