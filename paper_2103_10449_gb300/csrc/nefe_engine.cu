@@ -68,6 +68,7 @@ struct nefe_ctx {
     void *d_F = nullptr, *d_xs = nullptr, *d_xa = nullptr, *d_xcs = nullptr, *d_sd0 = nullptr, *d_xi = nullptr;
     void *d_shd = nullptr, *d_P = nullptr, *d_spill = nullptr;
     int *d_shj = nullptr, *d_shn = nullptr, *d_rtiles = nullptr, *d_rcount = nullptr, *d_rcbase = nullptr;
+    int* d_any = nullptr;    // context-wide rebuild flag words (Bufs::any_rebuild)
     int *d_uf_nbr = nullptr, *d_uf_cnt = nullptr, *d_uf_tiles = nullptr;
     int* d_lacc = nullptr;   // scatter-form force accumulators (FP32 contexts)
     void* d_uf_F = nullptr;
@@ -416,6 +417,8 @@ int setup(nefe_ctx* c) {
     if ((rc = dalloc(c, &c->d_rtiles, sizeof(int) * tile_sys.size()))) return rc;
     if ((rc = dalloc(c, &c->d_rcount, sizeof(int)))) return rc;
     if ((rc = dalloc(c, &c->d_rcbase, sizeof(int) * (size_t)(nsys + 1)))) return rc;
+    if ((rc = dalloc(c, &c->d_any, sizeof(int) * 2))) return rc;
+    NEFE_CU(cudaMemset(c->d_any, 0, sizeof(int) * 2));
     if ((rc = dalloc(c, &c->d_q, sizeof(int4) * N))) return rc;
     if ((rc = dalloc(c, &c->d_cell_of, sizeof(int) * N))) return rc;
     if ((rc = dalloc(c, &c->d_perm, sizeof(int) * N))) return rc;
@@ -482,7 +485,7 @@ int setup(nefe_ctx* c) {
     b.x = c->d_x; b.v = c->d_v; b.dhi = c->d_dhi; b.dlo = c->d_dlo; b.r0 = c->d_r0; b.F = c->d_F;
     b.xs = c->d_xs; b.xa = c->d_xa; b.xcs = c->d_xcs; b.sd0 = c->d_sd0; b.xi = c->d_xi;
     b.shd = c->d_shd; b.shj = c->d_shj; b.shn = c->d_shn; b.P = c->d_P; b.spill = c->d_spill;
-    b.rtiles = c->d_rtiles; b.rcount = c->d_rcount; b.rcbase = c->d_rcbase;
+    b.rtiles = c->d_rtiles; b.rcount = c->d_rcount; b.rcbase = c->d_rcbase; b.any_rebuild = c->d_any;
     b.q = c->d_q; b.cell_of = c->d_cell_of; b.perm = c->d_perm; b.cell_start = c->d_cell_start;
     b.cell_count = c->d_cell_count; b.cell_cursor = c->d_cell_cursor; b.nbr = c->d_nbr; b.cnt = c->d_cnt;
     b.cap = c->cap; b.ntot = c->ntot; b.dt = c->dt; b.swc = c->d_swc; b.pairs = c->d_pairs;

@@ -381,6 +381,14 @@ __global__ void __launch_bounds__(kTile) k_cells_count(Bufs b) {
 // full width where many small builds, one per step, each pay their latency.
 __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
     __shared__ int cnt;
+    // no flag set anywhere this step (b.any_rebuild[0], written wherever a flag is): empty worklist
+    if (!force_all && b.any_rebuild && *(volatile int*)b.any_rebuild == 0) {
+        if (threadIdx.x == 0) {
+            *b.rcount = 0;
+            if (b.rcbase) b.rcbase[nsys] = 0;
+        }
+        return;
+    }
     if (threadIdx.x == 0) cnt = 0;
     if (b.rebuild_all && !force_all) {
         int any = 0;
@@ -1315,10 +1323,11 @@ __device__ __forceinline__ void comp_add(T& hi, T& lo, T d) {
 // displacement, updated in place.  Shared by k_kick_drift and by the epilogue that moves the
 // atoms for the next step (systems without a barostat), so both do the same operations.
 // xa: the atom's mirror at the last build (loaded by the caller together with its other operands).
+// any: the context-wide word that records that some system's flag was set (or NULL).
 template <typename T>
 __device__ __forceinline__ void drift_atom(const Bufs& b, const DevSys& S, const DevState& st, int i,
                                            const typename V4<T>::t& xa, const T (&vk)[3], bool move,
-                                           T (&dh)[3], T (&dl)[3], int flag_set, int* flag,
+                                           T (&dh)[3], T (&dl)[3], int flag_set, int* flag, int* any,
                                            unsigned long long kstep, T (&z)[3]) {
     using T4 = typename V4<T>::t;
     const size_t N = b.ntot;
@@ -1353,7 +1362,10 @@ __device__ __forceinline__ void drift_atom(const Bufs& b, const DevSys& S, const
         const T dd = hmoved ? m[k] - xav[k] * pick<T>(st.h[k] / st.hb[k], st.rho_f[k]) : dh[k] + dl[k];
         dd2 += dd * dd;
     }
-    if (dd2 > pick<T>(st.thr2, st.thr2_f) && !flag_set) atomicOr(flag, 1);
+    if (dd2 > pick<T>(st.thr2, st.thr2_f) && !flag_set) {
+        atomicOr(flag, 1);
+        if (any) atomicOr(any, 1);
+    }
     z[0] = z[1] = z[2] = (T)0;
     if (S.thermo) {
         Noise<T>::xi3(S.seed, (uint64_t)S.rng_id, (uint64_t)kstep, (uint64_t)(i - S.off), z);
@@ -1392,7 +1404,8 @@ __global__ void __launch_bounds__(kTile) k_kick_drift(Bufs b, int mode, int skip
                 V[k * N + i] = vk[k];
             }
         }
-        drift_atom<T>(b, S, st, i, xa, vk, mode == 1, dh, dl, st.rebuild, &st.rebuild, (unsigned long long)st.k,
+        drift_atom<T>(b, S, st, i, xa, vk, mode == 1, dh, dl, st.rebuild, &st.rebuild, b.any_rebuild,
+                      (unsigned long long)st.k,
                       xs_sum);
     }
     block_sum_to_acc<T, 3>(xs_sum, b.acc + (size_t)ta.sys * ACC_N * kSlots, ACC_XI, &st.err);
@@ -2202,7 +2215,8 @@ __global__ void __launch_bounds__(kTile) k_finish(Bufs b, int fuse) {
                 vk[k] = vo[k] + ck * Fo[k];
                 V[k * N + i] = vk[k];
             }
-            drift_atom<T>(b, S, st, i, xa, vk, true, dh, dl, 0, &gst.rebuild_next, (unsigned long long)st.k + 1ULL,
+            drift_atom<T>(b, S, st, i, xa, vk, true, dh, dl, 0, &gst.rebuild_next,
+                          b.any_rebuild ? b.any_rebuild + 1 : nullptr, (unsigned long long)st.k + 1ULL,
                           zn);
         }
     }
@@ -2503,6 +2517,12 @@ __global__ void __launch_bounds__(kTile) k_group(Bufs b, const DevGroup* groups,
             const uint32_t* dp = reinterpret_cast<const uint32_t*>(&spr);
             for (int w = threadIdx.x; w < wp; w += blockDim.x) gp[w] = dp[w];
         }
+    }
+    // the context-wide flag word: this step's flags start from the fused epilogue's (carry) or
+    // from none; the next step's word is cleared (block 0 only; no other block touches it)
+    if (mode == 1 && b.any_rebuild && blockIdx.x == 0 && threadIdx.x == 0) {
+        b.any_rebuild[0] = carry ? b.any_rebuild[1] : 0;
+        b.any_rebuild[1] = 0;
     }
     if (mode != 2) {
         for (int mi = 0; mi < nm; ++mi) {

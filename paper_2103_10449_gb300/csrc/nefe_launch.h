@@ -63,6 +63,8 @@ struct Bufs {
     void* uf_F;              // [ntot] UF force and atom energy of the step (T4)
     const int* uf_tiles;     // tiles of the UF systems (per-step UF kernel), or NULL: every tile
     int* lacc;               // [ntot][4] int32 force accumulators of the scatter form (2^-21 eV/A)
+    int* any_rebuild;        // engine: [0] some system's rebuild flag is set this step, [1] some
+                             // rebuild_next is set (fused epilogue); NULL in the stateless calls
     int rebuild_all;         // engine: when any system's list is stale, every system rebuilds (one
                              // full-width build instead of many narrow ones)
 };
