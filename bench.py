@@ -41,8 +41,11 @@ T_SW = 1000.0
 K_E = 5.0
 NSCHED = 20000
 MD_STEPS = 32       # MD steps per timed step (one graph replay)
-SKIN = 0.7          # Verlet skin (A): fewest list builds for the least row growth at 1000 K (measured
-                    # over 0.5-1.1 A); it changes no result beyond the FP32 list band
+SKIN = 0.7          # Verlet skin (A) of the dCCI, reversible-scaling and comparator contexts
+FL_SKIN = 1.6       # Verlet skin (A) of the timed Frenkel-Ladd crystal: with rcs = 5.37 A the rows hold the
+                    # first three neighbour shells (28 entries; the fourth lies at 5.43 A), and an atom of
+                    # the 1000 K crystal rarely moves skin/2 = 0.8 A, so lists are almost never rebuilt
+                    # (measured 0.7 / 1.0 / 1.2 / 1.4 / 1.6 A); lists are exact at any skin
 # Algorithmic bytes per atom of the two force passes (FP32 path, Frenkel-Ladd), m = mean
 # in-cutoff shell size, nbar = mean Verlet row length:
 #   pass A (edges): own mirror 16 + row length 4 + row 4 nbar + shell indices 4 m + leg forces
@@ -589,7 +592,7 @@ def main():
     ap.add_argument("--equil", type=int, default=3000,
                     help="untimed MD steps before warm-up (thermalises the crystals)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparators, e2e and CPU baseline")
-    ap.add_argument("--skin", type=float, default=SKIN, help="Verlet skin (A) of the timed context")
+    ap.add_argument("--skin", type=float, default=FL_SKIN, help="Verlet skin (A) of the timed context")
     ap.add_argument("--tuning", default=None,
                     help="pass A,pass B lanes per atom[,rebuild policy] instead of autotuning (e.g. to profile a chosen "
                          "configuration)")
@@ -720,7 +723,7 @@ def main():
                                             ("fp32_single_replica", 1, N.NEFE_FP32, 20, 1000),
                                             ("fp64_batched", R, N.NEFE_FP64, 3, 200)):
             s2 = torch.cuda.Stream()
-            c2, na = build_context(N, reps, prec, stream=s2)
+            c2, na = build_context(N, reps, prec, stream=s2, skin=args.skin)   # same list radius
             c2.run(eq)
             c2.autotune()
             for _ in range(2):

@@ -59,6 +59,7 @@ extern "C" {
 #define NEFE_ERR_DEGEN          0x8u   /* dCCI singular update (see NEFE_EDEGEN)         */
 #define NEFE_ERR_BOX            0x10u  /* box below 2 (rc + skin) or cell grid too large */
 #define NEFE_ERR_CELL           0x20u  /* cell occupancy inconsistent with the atom count   */
+#define NEFE_ERR_TIMEOUT        0x40u  /* a grid barrier of the list rebuild gave up waiting */
 
 /* Precision of the force kernel.  Positions, box, energies, virial and work are FP64 in
  * both; NEFE_FP32 evaluates the pair and triplet arithmetic in FP32.                   */
@@ -374,7 +375,10 @@ NEFE_API int nefe_setup(nefe_ctx* ctx);
 /* Advances every system by nsteps (asynchronous; replays a captured CUDA graph of the
  * step sequence in chunks). */
 NEFE_API int nefe_run(nefe_ctx* ctx, long nsteps);
-/* Blocks until the context's stream is idle; returns NEFE_ECUDA on an asynchronous error. */
+/* Blocks until the context's stream is idle; returns NEFE_ECUDA on an asynchronous error, and
+ * NEFE_ETIMEOUT if a grid barrier of the list rebuild gave up waiting since the last call (its
+ * systems then carry NEFE_ERR_TIMEOUT; the barrier is reset, the lists of that step are not
+ * valid: reload a checkpoint or set the state again). */
 NEFE_API int nefe_sync(nefe_ctx* ctx);
 
 /* Blocking reads (they synchronise the stream first).  nefe_get_results: the dynamical work W
@@ -401,11 +405,10 @@ NEFE_API int nefe_load(nefe_ctx* ctx, const char* path);
 
 /* Times the variants of both force passes on the current state and keeps the fastest:
  * pass A with 1 (one thread per atom), 4, 8, 16 or 32 lanes per atom (FP64: 8, 16, 32),
- * pass B with 1, 2, 4 or 8 lanes per atom, the list build with 8, 16 or 32, and the rebuild
- * policy (nefe_set_rebuild_policy).  Each force pass is first timed alone; then the two fastest
- * pass-A variants with every pass-B variant, and with the best pair each list-build variant and
- * each rebuild policy, run as real steps on a device snapshot of the state, restored afterwards
- * (the run
+ * pass B with 1, 2, 4 or 8 lanes per atom, and the rebuild policy (nefe_set_rebuild_policy); the
+ * list build keeps its form (nefe_set_list_tuning).  Each force pass is first timed alone; then
+ * the two fastest pass-A variants with every pass-B variant, and with the best pair each rebuild
+ * policy, run as real steps on a device snapshot of the state, restored afterwards (the run
  * continues bit for bit as without the call; the snapshot needs about as much free device
  * memory as the state, and without it the kernel-level choice stands).  nefe_get_tuning
  * reports pass A's lanes and the time per MD step of the chosen pair (kernel-level: the two
@@ -419,6 +422,14 @@ NEFE_API int nefe_get_lanes(nefe_ctx* ctx, int lanes[3]);
 NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
 /* Fixes the list build's form: 0 = one warp per cell (the default), or 8, 16, 32 lanes per atom. */
 NEFE_API int nefe_set_list_tuning(nefe_ctx* ctx, int lanes_per_atom);
+/* Failure detection of the time-bounded grid barrier (the one device-side wait of the library,
+ * in the engine's single-launch list rebuild; the paper has no counterpart).  Launches a small
+ * grid whose barrier can never complete (it expects one block more than it has), with a limit of
+ * limit_ms milliseconds: every block must give up, record the timeout and return, so the call
+ * returns NEFE_ETIMEOUT and the device stays usable.  NEFE_OK would mean the wait did not end by
+ * its limit (never expected); NEFE_EINVAL for limit_ms outside (0, 1000]. */
+NEFE_API int nefe_check_barrier_timeout(int device, double limit_ms);
+
 /* Rebuild policy of the Verlet lists (the skin criterion of the list, Sec. 4's MD setup; the
  * paper itself does not discuss lists).  all = 0: each system rebuilds when one of its own atoms
  * has moved more than skin/2 since its last build.  all = 1: on a step where any system needs

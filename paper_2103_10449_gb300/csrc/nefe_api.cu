@@ -333,6 +333,14 @@ int nefe_uf_forces(const double* x, int n, const double box[3], double rcs, doub
     return NEFE_OK;
 }
 
+int nefe_check_barrier_timeout(int device, double limit_ms) {
+    if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) return fail(NEFE_EINVAL, "limit_ms must be in (0, 1000]");
+    NEFE_CU(cudaSetDevice(device));
+    const int r = check_barrier_timeout(limit_ms);
+    if (r < 0) return fail(NEFE_ECUDA, "barrier check: CUDA error");
+    return r ? fail(NEFE_ETIMEOUT, "the barrier gave up by its limit (expected)") : NEFE_OK;
+}
+
 int nefe_langevin_noise(uint64_t seed, uint64_t sys_id, uint64_t step, int n, int precision,
                         double* xi, void* stream) {
     NvtxRange nvtx_("nefe_langevin_noise");

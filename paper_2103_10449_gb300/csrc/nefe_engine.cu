@@ -92,6 +92,7 @@ struct nefe_ctx {
     long launches = 0;
     long graph_launches = 0;     // kernel launches in one replay of the captured graph
     bool any_baro = false;       // some system has a barostat (k_kick_drift has work every step)
+    int coop_blocks = 0;         // grid of the single-launch rebuild (0: the kernel sequence instead)
     bool profiling = false;
     std::vector<cudaEvent_t> ev0, ev1, ev2;   // around the force passes of the captured graph
     std::vector<int> chunk_tile0, chunk_ntile;
@@ -185,8 +186,14 @@ void enqueue_step(nefe_ctx* c, int slot = -1, bool first = true, bool last = tru
     // with every system moved by the previous epilogue there is nothing left for k_kick_drift
     if (!(fused && !first && !c->any_baro))
         launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches, fused && !first);
-    launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
-    if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
+    // the rebuild: one cooperative launch (worklist, cells, lists between grid barriers), or the
+    // kernel sequence where the list build has lanes per atom or UF rows are built too
+    if (c->coop_blocks > 0 && c->llanes == 0 && c->n_uf_tiles == 0) {
+        launch_rebuild_coop(c->b, c->prec, c->coop_blocks, c->nsys, c->stream, &c->launches);
+    } else {
+        launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
+        if (c->n_uf_tiles > 0) launch_uf_list(c->b, c->prec, c->ntiles, c->stream, &c->launches);
+    }
     enqueue_forces(c, FM_STEP, slot, fused && !last);
 }
 
@@ -417,8 +424,10 @@ int setup(nefe_ctx* c) {
     if ((rc = dalloc(c, &c->d_rtiles, sizeof(int) * tile_sys.size()))) return rc;
     if ((rc = dalloc(c, &c->d_rcount, sizeof(int)))) return rc;
     if ((rc = dalloc(c, &c->d_rcbase, sizeof(int) * (size_t)(nsys + 1)))) return rc;
-    if ((rc = dalloc(c, &c->d_any, sizeof(int) * 2))) return rc;
-    NEFE_CU(cudaMemset(c->d_any, 0, sizeof(int) * 2));
+    // [0], [1] rebuild flags of this and the next step, [2] barrier timeout, [3] barrier word
+    if ((rc = dalloc(c, &c->d_any, sizeof(int) * 4))) return rc;
+    NEFE_CU(cudaMemset(c->d_any, 0, sizeof(int) * 4));
+    c->coop_blocks = rebuild_coop_blocks(c->prec);
     if ((rc = dalloc(c, &c->d_q, sizeof(int4) * N))) return rc;
     if ((rc = dalloc(c, &c->d_cell_of, sizeof(int) * N))) return rc;
     if ((rc = dalloc(c, &c->d_perm, sizeof(int) * N))) return rc;
@@ -730,6 +739,14 @@ int nefe_sync(nefe_ctx* c) {
     int rc = set_device(c);
     if (rc) return rc;
     NEFE_CU(cudaStreamSynchronize(c->stream));
+    if (c->d_any) {
+        int w[2] = {0, 0};
+        NEFE_CU(cudaMemcpy(w, c->d_any + 2, sizeof(w), cudaMemcpyDeviceToHost));
+        if (w[0]) {
+            NEFE_CU(cudaMemset(c->d_any + 2, 0, 2 * sizeof(int)));   // the barrier starts afresh
+            return fail(NEFE_ETIMEOUT, "a grid barrier of the list rebuild gave up waiting");
+        }
+    }
     return NEFE_OK;
 }
 
@@ -992,28 +1009,9 @@ static int refine_in_steps(nefe_ctx* c, const std::vector<std::pair<double, int>
             copy(false);
         }
     }
-    // then the list build's lanes with the chosen pair (its cost is only seen in real steps,
-    // where a few systems rebuild at a time)
-    int best_l = c->llanes;
-    for (int ll : {0, 8, 16, 32}) {
-        if (rc != NEFE_OK || ll == best_l) continue;
-        c->lanes = best_a;
-        c->glanes = best_b;
-        c->llanes = ll;
-        c->b.list_lanes = ll;
-        drop_graph(c);
-        if ((rc = nefe_run(c, kGraphSteps))) break;
-        cudaEventRecord(e0, c->stream);
-        if ((rc = nefe_run(c, 2 * kGraphSteps))) break;
-        cudaEventRecord(e1, c->stream);
-        float ms = 1e30f;
-        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        const double us = 1000.0 * ms / (2 * kGraphSteps);
-        if (us < best) { best = us; best_l = ll; }
-        copy(false);
-    }
-    c->llanes = best_l;
-    c->b.list_lanes = best_l;
+    // The list build keeps its form (one warp per cell, the default: it runs as the single-launch
+    // cooperative rebuild): timed over a few real steps its forms rank by noise whenever no list
+    // happens to be rebuilt in the window.
     // then the rebuild policy with the chosen lanes (its effect too is seen only in real steps)
     int best_r = c->rebuild_all;
     if (rc == NEFE_OK) {

@@ -379,7 +379,8 @@ __global__ void __launch_bounds__(kTile) k_cells_count(Bufs b) {
 // of all are set here, so the later rebuild kernels see them): rebuilding a list early never
 // changes what the force passes compute, and one build over the whole batch runs its kernels at
 // full width where many small builds, one per step, each pay their latency.
-__global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
+// The worklist of one step, built by one block (any multiple of 32 threads up to 256).
+__device__ void build_worklist(const Bufs& b, int nsys, int force_all) {
     __shared__ int cnt;
     // no flag set anywhere this step (b.any_rebuild[0], written wherever a flag is): empty worklist
     if (!force_all && b.any_rebuild && *(volatile int*)b.any_rebuild == 0) {
@@ -427,9 +428,9 @@ __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int forc
     if (threadIdx.x == 0) *b.rcount = cnt;
     if (b.rcbase) {   // first worklist cell of each system: exclusive scan of the flagged cell counts
         __shared__ int wsum[8];
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
         int carry = 0;
-        for (int base = 0; base < nsys; base += 256) {
+        for (int base = 0; base < nsys; base += (int)blockDim.x) {
             const int s = base + (int)threadIdx.x;
             int v = 0;
             if (s < nsys) {
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int forc
             if (lane == 31) wsum[w] = incl;
             __syncthreads();
             int woff = 0, tot = 0;
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < nw; ++k) {
                 if (k < w) woff += wsum[k];
                 tot += wsum[k];
             }
@@ -455,6 +456,10 @@ __global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int forc
         }
         if (threadIdx.x == 0) b.rcbase[nsys] = carry;
     }
+}
+
+__global__ void __launch_bounds__(256) k_rebuild_list(Bufs b, int nsys, int force_all) {
+    build_worklist(b, nsys, force_all);
 }
 
 // R2: exclusive scan of system s's cell occupancy by one block (blockDim a multiple of 32, at
@@ -1068,8 +1073,7 @@ __device__ __forceinline__ void nlist_cell(const Bufs& b, int s, int c, CellList
 // flagged systems in system order (rcbase[s] = first worklist cell of system s, rcbase[nsys] =
 // their number); without one (stateless calls, one system), every cell of system 0.
 template <typename T>
-__global__ void __launch_bounds__(kTile, 8) k_nlist_cell(Bufs b, int nsys) {
-    __shared__ CellListShared<T> shm[kTile / 32];
+__device__ void nlist_cells_of_grid(const Bufs& b, int nsys, CellListShared<T>* shm) {
     const int lane = threadIdx.x & 31;
     CellListShared<T>& sh = shm[threadIdx.x >> 5];
     const int nw = gridDim.x * (kTile / 32);
@@ -1099,6 +1103,94 @@ __global__ void __launch_bounds__(kTile, 8) k_nlist_cell(Bufs b, int nsys) {
         }
         nlist_cell<T>(b, s, g - (b.rcbase ? b.rcbase[s] : 0), sh, lane);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile, 8) k_nlist_cell(Bufs b, int nsys) {
+    __shared__ CellListShared<T> shm[kTile / 32];
+    nlist_cells_of_grid<T>(b, nsys, shm);
+}
+
+// ------------------------------------------------------------------------------------
+// The engine's whole rebuild in one cooperative launch (all blocks resident): worklist (block
+// 0), cell count, scan, fill and list build, separated by grid barriers.  On a step where no list
+// is stale every block returns at once, so the step pays one near-empty launch instead of five.
+//
+// Grid barrier: one 32-bit word; block 0 adds 2^31 - (nblocks - 1), every other block adds 1, so
+// the word's top bit flips exactly when the last block arrives and its low bits return to what
+// they were (the word needs no reset between barriers or launches).  Each block waits for the
+// top bit it saw to flip, for at most kBarrierNs of %globaltimer; a block that gives up sets the
+// context's timeout word and NEFE_ERR_TIMEOUT in every system and returns (the host then reports
+// NEFE_ETIMEOUT and resets the words).  The launch is cooperative, so the wait never depends on a
+// block that is not resident.
+// ------------------------------------------------------------------------------------
+constexpr unsigned long long kBarrierNs = 1000000000ULL;   // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false (in every thread of the block) when the wait gave up.
+__device__ bool grid_barrier(unsigned* word, int* timeout, unsigned long long limit_ns, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+        __threadfence();
+        const unsigned old = atomicAdd(word, add);
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        while (((*(volatile unsigned*)word ^ old) & 0x80000000u) == 0u) {
+            if (global_ns() - t0 > limit_ns) {
+                ok = 0;
+                atomicOr(timeout, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ void flag_timeout(const Bufs& b, int nsys) {
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) atomicOr(&b.st[s].err, NEFE_ERR_TIMEOUT);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile, 8) k_rebuild_coop(Bufs b, int nsys) {
+    __shared__ CellListShared<T> shm[kTile / 32];
+    // no flag set anywhere this step: the word is written only by the kernels before this one
+    if (*(volatile int*)b.any_rebuild == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *b.rcount = 0;
+            b.rcbase[nsys] = 0;
+        }
+        return;
+    }
+    unsigned* bar = reinterpret_cast<unsigned*>(b.any_rebuild + 3);
+    int* tmo = b.any_rebuild + 2;
+    const unsigned nb = gridDim.x;
+    if (blockIdx.x == 0) build_worklist(b, nsys, 0);
+    if (!grid_barrier(bar, tmo, kBarrierNs, nb)) { flag_timeout(b, nsys); return; }
+    NEFE_FOR_TILES(b, cells_count_tile<T>(b, tile));
+    if (!grid_barrier(bar, tmo, kBarrierNs, nb)) { flag_timeout(b, nsys); return; }
+    for (int sy = blockIdx.x; sy < nsys; sy += gridDim.x)
+        if (b.st[sy].rebuild) scan_system_cells(b, sy);
+    if (!grid_barrier(bar, tmo, kBarrierNs, nb)) { flag_timeout(b, nsys); return; }
+    NEFE_FOR_TILES(b, cells_fill_tile<T>(b, tile));
+    if (!grid_barrier(bar, tmo, kBarrierNs, nb)) { flag_timeout(b, nsys); return; }
+    nlist_cells_of_grid<T>(b, nsys, shm);
+}
+
+// Test of the barrier's time limit: a grid whose barrier expects one block more than it has
+// (nothing will ever complete it), with a short limit; every block gives up and sets *timeout.
+__global__ void __launch_bounds__(kTile) k_barrier_selftest(unsigned* word, int* timeout, unsigned long long ns) {
+    grid_barrier(word, timeout, ns, gridDim.x + 1u);
 }
 
 // ------------------------------------------------------------------------------------
@@ -2628,6 +2720,49 @@ void launch_cells_and_list(const Bufs& b, int precision, int ntiles, int nsys, i
         else k_nlist<float, 32><<<g, kTile, 0, s>>>(b);
     }
     if (launches) *launches += 1;
+}
+
+int rebuild_coop_blocks(int precision) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = precision == NEFE_FP64
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild_coop<double>, kTile, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild_coop<float>, kTile, 0);
+    if (e != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return min(per_sm * sms, kRebuildBlocks);
+}
+
+void launch_rebuild_coop(const Bufs& b, int precision, int blocks, int nsys, cudaStream_t s, long* launches) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kTile);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // every block resident: the grid barriers can complete
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (precision == NEFE_FP64) cudaLaunchKernelEx(&cfg, k_rebuild_coop<double>, b, nsys);
+    else cudaLaunchKernelEx(&cfg, k_rebuild_coop<float>, b, nsys);
+    if (launches) *launches += 1;
+}
+
+int check_barrier_timeout(double limit_ms) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, 2 * sizeof(int)) != cudaSuccess) return -2;
+    cudaMemset(p, 0, 2 * sizeof(int));
+    unsigned* word = static_cast<unsigned*>(p);
+    int* tmo = static_cast<int*>(p) + 1;
+    k_barrier_selftest<<<4, kTile>>>(word, tmo, (unsigned long long)(limit_ms * 1e6));
+    int h = 0;
+    const cudaError_t e = cudaMemcpy(&h, tmo, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(p);
+    if (e != cudaSuccess) return -3;
+    return h ? 1 : 0;
 }
 
 void launch_aos_soa(const double* src, double* dst, int n, int to_soa, cudaStream_t s) {

@@ -113,6 +113,14 @@ void launch_mirror(const Bufs& b, int precision, int ntiles, cudaStream_t s, lon
 void launch_noise(unsigned long long seed, unsigned long long sys_id, unsigned long long step,
                   int n, int precision, double* xi, cudaStream_t s);
 
+// The engine's single-launch rebuild (cooperative; see k_rebuild_coop): the largest grid whose
+// blocks are all resident (0 if it cannot be launched), and its launch.
+int rebuild_coop_blocks(int precision);
+void launch_rebuild_coop(const Bufs& b, int precision, int blocks, int nsys, cudaStream_t s, long* launches);
+// Runs the barrier time-limit check on the current device: 1 timed out (expected), 0 did not,
+// negative on a CUDA error.
+int check_barrier_timeout(double limit_ms);
+
 bool lanes_supported(int lanes);
 // (n,3) row-major <-> SoA (to_soa = 1: aos -> soa).
 void launch_aos_soa(const double* src, double* dst, int n, int to_soa, cudaStream_t s);

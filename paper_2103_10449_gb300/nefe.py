@@ -17,6 +17,7 @@ from . import build as _build
 NEFE_OK, NEFE_EINVAL, NEFE_ENOMEM, NEFE_ECUDA, NEFE_EOVERFLOW = 0, -1, -2, -3, -4
 NEFE_ENAN, NEFE_EDEGEN, NEFE_ETIMEOUT, NEFE_ESTATE = -6, -7, -8, -9
 NEFE_ERR_NBR_OVERFLOW, NEFE_ERR_SHELL_OVERFLOW, NEFE_ERR_NAN, NEFE_ERR_DEGEN, NEFE_ERR_BOX = 1, 2, 4, 8, 16
+NEFE_ERR_CELL, NEFE_ERR_TIMEOUT = 32, 64
 NEFE_FP32, NEFE_FP64 = 0, 1
 NEFE_POT_SW, NEFE_POT_EINSTEIN, NEFE_POT_UF = 0, 1, 2
 NEFE_REF_EINSTEIN, NEFE_REF_UF = 0, 1
@@ -142,6 +143,7 @@ SIGNATURES = {
     "nefe_get_lanes": [_vp, _c_int_p],
     "nefe_set_list_tuning": [_vp, ctypes.c_int],
     "nefe_set_rebuild_policy": [_vp, ctypes.c_int],
+    "nefe_check_barrier_timeout": [ctypes.c_int, ctypes.c_double],
     "nefe_get_rebuild_policy": [_vp, _c_int_p],
     "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
     "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
@@ -281,6 +283,12 @@ def nefe_sw_dual(x, w, n, box, rcs, nbr, cnt, cap, prm, dtheta, f, fd, out16, st
 def nefe_langevin_noise(seed, sys_id, step, n, precision, xi, stream=None):
     _check(load().nefe_langevin_noise(int(seed), int(sys_id), int(step), int(n), int(precision), _ptr(xi),
                                       _stream(stream)))
+
+
+def nefe_check_barrier_timeout(device=0, limit_ms=50.0):
+    """Return code of the grid barrier's time-limit check: NEFE_ETIMEOUT when the barrier that can
+    never complete gave up by its limit (the expected outcome), NEFE_OK otherwise."""
+    return load().nefe_check_barrier_timeout(int(device), float(limit_ms))
 
 
 # ---------------------------------------------------------------------- context API

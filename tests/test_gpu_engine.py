@@ -123,3 +123,20 @@ def test_debug_bounds_build_runs_the_same_trajectory():
         out[flag] = vals.split()
     assert out["0"] == out["1"]
     assert out["1"][1] == "0"
+
+
+def test_grid_barrier_gives_up_by_its_time_limit():
+    """Failure detection of the one device-side wait (the grid barriers of the single-launch list
+    rebuild): a barrier that can never complete must end every waiting block by its limit and
+    report NEFE_ETIMEOUT; the device stays usable (an engine run afterwards is error free)."""
+    import time
+    from paper_2103_10449_gb300 import nefe as N
+    t0 = time.perf_counter()
+    rc = N.nefe_check_barrier_timeout(0, 50.0)
+    assert rc == N.NEFE_ETIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    ctx, n = _ctx(N, 2, precision=0)
+    ctx.run(64)
+    ctx.sync()
+    assert all(r["error"] == 0 for r in ctx.results_all())
+    ctx.close()
