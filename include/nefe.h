@@ -422,6 +422,15 @@ NEFE_API int nefe_get_lanes(nefe_ctx* ctx, int lanes[3]);
 NEFE_API int nefe_set_gather_tuning(nefe_ctx* ctx, int lanes_per_atom);
 /* Fixes the list build's form: 0 = one warp per cell (the default), or 8, 16, 32 lanes per atom. */
 NEFE_API int nefe_set_list_tuning(nefe_ctx* ctx, int lanes_per_atom);
+/* The engine's list rebuild as one cooperative launch (on = 1: worklist, cell count, scan, fill
+ * and list build in one kernel whose phases are separated by time-bounded grid barriers; its
+ * blocks return at once on a step without a stale list) or as the kernel sequence (on = 0, the
+ * default).  Both build the same lists bit for bit.  On this GPU the cooperative node of the step
+ * graph costs more per step (measured 244 against 237 us per MD step on the benchmark workload)
+ * than the four launches it replaces, hence the default.  Applies when the list build runs one
+ * warp per cell and no system has a Uhlenbeck-Ford term.  NEFE_EINVAL for other values. */
+NEFE_API int nefe_set_cooperative_rebuild(nefe_ctx* ctx, int on);
+
 /* Failure detection of the time-bounded grid barrier (the one device-side wait of the library,
  * in the engine's single-launch list rebuild; the paper has no counterpart).  Launches a small
  * grid whose barrier can never complete (it expects one block more than it has), with a limit of

@@ -92,7 +92,8 @@ struct nefe_ctx {
     long launches = 0;
     long graph_launches = 0;     // kernel launches in one replay of the captured graph
     bool any_baro = false;       // some system has a barostat (k_kick_drift has work every step)
-    int coop_blocks = 0;         // grid of the single-launch rebuild (0: the kernel sequence instead)
+    int coop_blocks = 0;         // grid of the single-launch rebuild (0: cannot be launched)
+    bool coop = false;           // rebuild as one cooperative launch (nefe_set_cooperative_rebuild)
     bool profiling = false;
     std::vector<cudaEvent_t> ev0, ev1, ev2;   // around the force passes of the captured graph
     std::vector<int> chunk_tile0, chunk_ntile;
@@ -188,7 +189,7 @@ void enqueue_step(nefe_ctx* c, int slot = -1, bool first = true, bool last = tru
         launch_kick_drift(c->b, c->prec, c->ntiles, 1, c->stream, &c->launches, fused && !first);
     // the rebuild: one cooperative launch (worklist, cells, lists between grid barriers), or the
     // kernel sequence where the list build has lanes per atom or UF rows are built too
-    if (c->coop_blocks > 0 && c->llanes == 0 && c->n_uf_tiles == 0) {
+    if (c->coop && c->coop_blocks > 0 && c->llanes == 0 && c->n_uf_tiles == 0) {
         launch_rebuild_coop(c->b, c->prec, c->coop_blocks, c->nsys, c->stream, &c->launches);
     } else {
         launch_cells_and_list(c->b, c->prec, c->ntiles, c->nsys, 0, c->stream, &c->launches);
@@ -1365,6 +1366,14 @@ int nefe_set_rebuild_policy(nefe_ctx* c, int all) {
     if (c->b.rebuild_all != all) drop_graph(c);   // the policy is captured in the step graph
     c->rebuild_all = all;
     c->b.rebuild_all = all;
+    return NEFE_OK;
+}
+
+int nefe_set_cooperative_rebuild(nefe_ctx* c, int on) {
+    if (!c) return fail(NEFE_EINVAL, "context is NULL");
+    if (on != 0 && on != 1) return fail(NEFE_EINVAL, "on must be 0 or 1");
+    if (c->coop != (on != 0)) drop_graph(c);     // the form is captured in the step graph
+    c->coop = on != 0;
     return NEFE_OK;
 }
 

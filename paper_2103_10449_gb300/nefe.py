@@ -144,6 +144,7 @@ SIGNATURES = {
     "nefe_set_list_tuning": [_vp, ctypes.c_int],
     "nefe_set_rebuild_policy": [_vp, ctypes.c_int],
     "nefe_check_barrier_timeout": [ctypes.c_int, ctypes.c_double],
+    "nefe_set_cooperative_rebuild": [_vp, ctypes.c_int],
     "nefe_get_rebuild_policy": [_vp, _c_int_p],
     "nefe_launch_count": [_vp, ctypes.POINTER(ctypes.c_long)],
     "nefe_set_state_all": [_vp, _c_dbl_p, _c_dbl_p],
@@ -427,6 +428,10 @@ class Context:
     def set_rebuild_policy(self, all_systems):
         """1: every system rebuilds its list on a step where any system needs it; 0: each on its own."""
         _check(self._L.nefe_set_rebuild_policy(self.h, int(all_systems)))
+
+    def set_cooperative_rebuild(self, on):
+        """1: the list rebuild as one cooperative launch with grid barriers; 0: the kernel sequence."""
+        _check(self._L.nefe_set_cooperative_rebuild(self.h, int(on)))
 
     def rebuild_policy(self):
         out = ctypes.c_int()

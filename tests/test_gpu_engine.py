@@ -125,6 +125,29 @@ def test_debug_bounds_build_runs_the_same_trajectory():
     assert out["1"][1] == "0"
 
 
+def test_cooperative_rebuild_builds_the_same_lists():
+    """The list rebuild as one cooperative launch (worklist, cells and lists between grid
+    barriers) and as the kernel sequence build the same lists, so the runs are bit for bit equal
+    -- under both rebuild policies, with rebuilds along the way."""
+    from paper_2103_10449_gb300 import nefe as N
+    for pol in (0, 1):
+        out = []
+        for coop in (0, 1):
+            ctx, n = _ctx(N, 3, precision=0)
+            ctx.set_tuning(0, None, 0)
+            ctx.set_rebuild_policy(pol)
+            ctx.set_cooperative_rebuild(coop)
+            ctx.run(200)
+            ctx.sync()
+            out.append(([ctx.results(s)["W"] for s in range(3)], [ctx.get_state(s)[0] for s in range(3)],
+                        ctx.list_stats(-1)[2]))
+            assert all(r["error"] == 0 for r in ctx.results_all())
+            ctx.close()
+        (wa, xa, ba), (wb, xb, bb) = out
+        assert ba == bb and ba > 5
+        assert wa == wb and all(np.array_equal(p, q) for p, q in zip(xa, xb))
+
+
 def test_grid_barrier_gives_up_by_its_time_limit():
     """Failure detection of the one device-side wait (the grid barriers of the single-launch list
     rebuild): a barrier that can never complete must end every waiting block by its limit and
