@@ -8,15 +8,22 @@
 //   k_kick_drift  v += dt/2 F/m; displacement since the last list build += dt phi v (+ the
 //                 affine box drift), kept as a compensated pair in the FP32 path; mirror
 //                 xs = x - q h; displacement test -> rebuild flag; thermostat noise + its sum.
+//                 In the scatter form this work is done by the previous step's epilogue for the
+//                 systems without a barostat (k_finish with fuse), and the kernel skips them.
 //   rebuild       (flagged systems) fold the displacement into the FP64 anchor, cell count ->
-//                 scan -> fill (with a cell-ordered copy of the mirror) -> Verlet list.
-//   k_edges       force pass A: in-cutoff shell of each atom, pair terms, and for each shell
-//                 edge the force its triplets exert on the leg atom (stored per edge); the
-//                 atom's own force, energy and virial.
-//   k_gather      force pass B: the atom's pass-A force plus the leg forces that the triplets
-//                 centred on its neighbours exert on it (a gather: no atomics, bitwise
-//                 reproducible); Einstein springs, lambda mixing, Langevin force with its
-//                 per-system mean removed, second half kick.
+//                 scan -> fill (with a cell-ordered copy of the mirror) -> Verlet list; as a
+//                 kernel sequence, or as one cooperative launch (k_rebuild_coop).
+//   k_edges1      force pass A, one thread per atom: in-cutoff shell of each atom, pair terms,
+//                 the shell's moments and the force the triplets centred on the atom exert on
+//                 each leg atom; in the scatter form (the FP32 default) every leg force and the
+//                 atom's own force go into int32 fixed-point accumulators (order independent).
+//                 k_edges: the lane-group variants (and the FP64 path), storing per edge.
+//   k_finish      the scatter form's epilogue: reads and clears the accumulators; Einstein
+//                 springs, lambda mixing, Langevin force with its per-system mean removed,
+//                 second half kick (and the next step's kick, drift and noise, see above).
+//   k_gather      force pass B of the gather form: the atom's pass-A force plus the leg forces
+//                 that the triplets centred on its neighbours exert on it, then the same
+//                 epilogue.
 //
 // Positions: the FP64 anchor x (positions at the last list build) plus the displacement
 // since then (FP64, or an FP32 value + FP32 compensation term, ~2^-48 relative).  The anchor
