@@ -58,6 +58,13 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     rc = L.nefe_create(ctypes.byref(h), 0, None, 7, 0.001, 0.5, 48)
     assert rc == N.NEFE_EINVAL
     assert L.nefe_destroy(None) == N.NEFE_OK
+    # context-level tuning calls reject a missing context; the barrier check rejects its limit
+    # before touching a device
+    assert L.nefe_set_rebuild_policy(None, 1) == N.NEFE_EINVAL
+    assert L.nefe_set_cooperative_rebuild(None, 1) == N.NEFE_EINVAL
+    assert L.nefe_check_barrier_timeout(0, 0.0) == N.NEFE_EINVAL
+    assert L.nefe_check_barrier_timeout(0, 5000.0) == N.NEFE_EINVAL
+    assert b"limit_ms" in L.nefe_last_error()
 
 
 def test_product_path_has_no_oracle_dependency():
